@@ -1,0 +1,223 @@
+/*
+ * hicops.h — C ABI of the GB300 peptide-database search library.
+ *
+ * The library implements the data-parallel hot path of the paper's
+ * superstep 3 ("Partial Database Peptide Search", Eq. 4, Supplementary
+ * Algorithm 3): for each experimental spectrum, the precursor-mass filter
+ * (filter_1), the shared-fragment-ion filter over a fragment-ion index
+ * (filter_2), hyperscore scoring of the candidates, the per-spectrum top-k
+ * heap and the score histogram (the "local null distribution" of the
+ * Sampling section), plus the linear-tail-fit e-value of superstep 4
+ * (Supplementary Algorithm 4).  The database it searches is built by
+ * superstep 1 ("Partial Database Construction", Supplementary Algorithm 1):
+ * in-silico tryptic digestion, modification variants (the 2^m variants of
+ * the Notation section), b/y model spectra and the fragment-ion index.
+ *
+ * Conventions for every entry point:
+ *   - Every call returns a hicops_status; no exception crosses the ABI.
+ *     On failure hicops_last_error() returns a thread-local message.
+ *   - The caller owns every input and output buffer.  The library copies
+ *     what it keeps; an index owns the device memory it allocated.
+ *   - Device work runs on the CUDA device that is current for the calling
+ *     thread when the index is built; later calls must use the same device.
+ *   - An index is immutable after it is built: concurrent hicops_search
+ *     calls on different streams are safe.
+ *
+ * Numeric readings (the paper leaves these open; they are fixed here):
+ *   - monoisotopic residue masses, H2O 18.010565 Da, proton 1.007276466812 Da;
+ *   - M = (sum of residue masses, left to right) + H2O; b_i = prefix_i +
+ *     proton; y_i = ((sum of residues i+1..L from the C terminus) + H2O) +
+ *     proton; fragment charge 1; FP64 throughout, no fused multiply-add;
+ *   - bin(mz) = floor(mz / bin_width_da) for frag_mz_min <= mz < frag_mz_max;
+ *     a query peak and a peptide ion are shared iff their bins are equal
+ *     (bin width = the fragment tolerance dF);
+ *   - a peptide's ion set is its set of distinct bins; a bin holding both a
+ *     b and a y ion of one peptide counts once, as b;
+ *   - pid = rank of the peptide in (neutral mass, sequence bytes,
+ *     modification state) ascending order;
+ *   - hyperscore HS = log10(nb!) + log10(ny!) + log10(S), S = sum of the
+ *     matched quantised intensities; the exact rank key is
+ *     K = LF[nb] + LF[ny] + LS[S] (int64, 2^32 fixed point, each term
+ *     rounded to nearest); top-k by (K desc, pid asc); histogram bin
+ *     min(255, K >> 31) over every candidate.
+ */
+#ifndef HICOPS_H
+#define HICOPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HICOPS_OK = 0,
+    HICOPS_EINVAL = 1,      /* invalid argument or unsupported parameter combination */
+    HICOPS_ENOMEM = 2,      /* host or device allocation failed */
+    HICOPS_ECUDA = 3,       /* a CUDA runtime call failed (message in hicops_last_error) */
+    HICOPS_ETIMEOUT = 4,    /* a bounded device or host wait ran out */
+    HICOPS_EOVERFLOW = 5,   /* a size limit of the index or of a counter would be exceeded */
+    HICOPS_EBUSY = 6,       /* resource temporarily unavailable (server admission) */
+    HICOPS_ECANCELLED = 7   /* request cancelled */
+} hicops_status;
+
+/* One modification rule (Notation section: each peptide expands into its
+ * modified forms).  residues: NUL-terminated residue letters.  fixed = 1
+ * applies delta_da to every such residue; fixed = 0 makes it variable with at
+ * most max_per_peptide modified positions per peptide.  A residue letter may
+ * carry at most one fixed and one variable rule. */
+typedef struct hicops_mod {
+    const char* residues;
+    double delta_da;
+    uint32_t max_per_peptide;
+    uint32_t fixed;
+} hicops_mod;
+
+/* Search parameters.  Digestion follows the paper's Experimental Setup
+ * (trypsin: cut after K/R unless followed by P; missed cleavages; length and
+ * neutral-mass limits).  Limits: 2 <= min_len <= max_len <= 64;
+ * 1 <= top_k <= 32; hist_bins == 256; 1 <= top_n_peaks <= 1024;
+ * 2*(max_len-1) * intensity_scale < 2^20 (per-peptide counters are packed
+ * into 32 bits); bin_width_da > 0; 0 < frag_mz_min < frag_mz_max and
+ * frag_mz_max / bin_width_da < 2^31. */
+typedef struct hicops_params {
+    uint32_t min_len, max_len, missed_cleavages, max_total_mods; /* max_total_mods 0 = no cap */
+    double min_mass, max_mass;
+    double frag_mz_min, frag_mz_max, bin_width_da;
+    uint32_t top_n_peaks, min_shared, top_k, hist_bins;
+    uint32_t intensity_scale, reserved;
+} hicops_params;
+
+/* Protein database: n_proteins sequences, protein i = seq[off[i] .. off[i+1]). */
+typedef struct hicops_proteins {
+    uint64_t n_proteins;
+    const char* seq;
+    const uint64_t* off;     /* [n_proteins + 1] */
+} hicops_proteins;
+
+/* A batch of experimental spectra (superstep 2's batches; a batch is the
+ * unit of one search call).  Peaks of spectrum q are
+ * mz/intensity[peak_off[q] .. peak_off[q+1]).  on_device = 1: every pointer
+ * of the batch AND every output pointer of the call are device pointers on
+ * the index's device, and the call is asynchronous on cuda_stream (results
+ * are ready when the stream reaches that point).  on_device = 0: host
+ * pointers; the call copies inputs in and results out and returns after the
+ * results are in the caller's buffers.  Invalid spectra (charge 0,
+ * non-finite precursor, negative tolerance, no peak inside
+ * [frag_mz_min, frag_mz_max), more than HICOPS_MAX_PEAKS raw peaks) do not
+ * fail the batch: their rows are padding and their histogram is empty. */
+typedef struct hicops_batch {
+    uint32_t n;
+    uint32_t on_device;
+    const uint64_t* peak_off;  /* [n + 1] */
+    const float* mz;
+    const float* intensity;
+    const double* prec_mz;     /* [n] precursor m/z */
+    const uint8_t* charge;     /* [n] precursor charge z */
+    const double* prec_tol_da; /* [n] precursor mass tolerance dM (Da) */
+    void* cuda_stream;         /* cudaStream_t; NULL = legacy default stream */
+} hicops_batch;
+
+#define HICOPS_MAX_PEAKS 4096
+
+/* One peptide-spectrum match.  Padding rows (fewer than top_k candidates or
+ * an invalid spectrum): pid = UINT32_MAX, key = INT64_MIN, nb = ny = 0,
+ * hyperscore = 0, evalue = +inf. */
+typedef struct hicops_psm {
+    uint32_t query;        /* spectrum index within the batch */
+    uint32_t pid;          /* peptide id (rank in the sorted database) */
+    uint8_t nb, ny;        /* shared b / y ion bins */
+    uint16_t reserved;
+    float hyperscore;      /* (float)(key * 2^-32) */
+    int64_t key;           /* exact rank key K */
+    double evalue;         /* survival-tail fit (FP64) */
+} hicops_psm;
+
+typedef struct hicops_index_stats {
+    uint64_t n_peptides;       /* P (database entries: sequence x modification state) */
+    uint64_t n_base_peptides;  /* distinct unmodified sequences */
+    uint64_t n_entries;        /* E: fragment-index entries (distinct bins summed over peptides) */
+    uint64_t n_bins;           /* number of m/z bins */
+    uint64_t device_bytes;     /* HBM held by the index */
+    uint64_t max_bucket;       /* largest bucket */
+    double host_ms;            /* digestion + variants + sort */
+    double device_ms;          /* fragment-index build on the GPU */
+} hicops_index_stats;
+
+typedef struct hicops_index hicops_index;
+
+/* Superstep 1 on the host only: digest, enumerate modification variants and
+ * sort into pid order.  Uses no GPU.  The result supports
+ * hicops_index_get_stats / hicops_peptide; hicops_index_upload makes it
+ * searchable.  Errors: HICOPS_EINVAL (parameters), HICOPS_EOVERFLOW (2^31
+ * peptides or more), HICOPS_ENOMEM. */
+hicops_status hicops_digest(const hicops_proteins* proteins, const hicops_mod* mods, uint32_t n_mods,
+                            const hicops_params* params, hicops_index** out);
+
+/* Builds the device fragment-ion index (model spectra -> integer bins ->
+ * radix-sorted CSR, pid ascending inside each bucket) on the current
+ * device.  Errors: HICOPS_ECUDA, HICOPS_ENOMEM, HICOPS_EOVERFLOW (2^32 or
+ * more entries in one bucket). */
+hicops_status hicops_index_upload(hicops_index* index);
+
+/* hicops_digest followed by hicops_index_upload. */
+hicops_status hicops_build_index(const hicops_proteins* proteins, const hicops_mod* mods, uint32_t n_mods,
+                                 const hicops_params* params, hicops_index** out);
+
+/* Searches one batch (superstep 3's filter_1, filter_2, score, heap; and the
+ * superstep-4 e-value).  Outputs: out_psm [n * top_k] rows, spectrum q at
+ * rows q*top_k .. q*top_k+top_k-1 in rank order; out_hist [n * 256] or NULL;
+ * out_nscored [n] (number of candidates, = sum of the histogram) or NULL.
+ * Errors: HICOPS_EINVAL (bad batch, spectrum over HICOPS_MAX_PEAKS peaks,
+ * index not uploaded), HICOPS_ECUDA, HICOPS_ENOMEM. */
+hicops_status hicops_search(hicops_index* index, const hicops_batch* batch, hicops_psm* out_psm,
+                            uint32_t* out_hist, uint32_t* out_nscored);
+
+/* Measurement helper: per spectrum, the precursor window [lo, hi), the
+ * number of retained peaks and the number of index entries inside the window
+ * over the retained peaks' buckets (H(q), the work of filter_2).  Any output
+ * may be NULL.  Same pointer rules as hicops_search. */
+hicops_status hicops_search_work(hicops_index* index, const hicops_batch* batch, uint32_t* out_lo,
+                                 uint32_t* out_hi, uint32_t* out_npeaks, uint64_t* out_hits);
+
+hicops_status hicops_index_get_stats(const hicops_index* index, hicops_index_stats* out);
+
+/* Peptide pid: sequence (NUL-terminated, truncated to cap-1 letters), neutral
+ * mass and the bitmask of positions carrying a variable modification (bit j =
+ * residue j, 0-based).  Host only. */
+hicops_status hicops_peptide(const hicops_index* index, uint32_t pid, char* seq, uint32_t cap,
+                             double* mass, uint64_t* modmask);
+
+/* Copies the fragment index to host buffers: off [n_bins + 1] bucket
+ * offsets and entries [n_entries] = pid << 1 | isY.  Either may be NULL. */
+hicops_status hicops_index_copy_csr(const hicops_index* index, uint64_t* off, uint32_t* entries);
+
+/* Per-phase device time of the last hicops_search on this index, measured
+ * with CUDA events recorded on the call's stream.  Measurement only: with
+ * timing enabled, concurrent searches on one index overwrite each other's
+ * events.  hicops_index_last_timing waits for the last call's end event. */
+typedef struct hicops_timing {
+    float prep_ms;      /* preprocessing + precursor window */
+    float plan_ms;      /* work-unit planning (segments, scan) */
+    float search_ms;    /* shared-peak accumulation, scoring, top-k, histogram */
+    float merge_ms;     /* top-k merge + e-value */
+    float total_ms;     /* first to last kernel of the call */
+} hicops_timing;
+
+hicops_status hicops_index_set_timing(hicops_index* index, int enable);
+hicops_status hicops_index_last_timing(hicops_index* index, hicops_timing* out);
+
+/* Number of CUDA kernels this library has launched in this process. */
+uint64_t hicops_kernel_launches(void);
+
+void hicops_index_free(hicops_index* index);
+
+/* Thread-local description of the last failure on this thread. */
+const char* hicops_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HICOPS_H */

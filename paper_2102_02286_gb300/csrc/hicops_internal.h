@@ -1,0 +1,80 @@
+// Internal declarations of the search library (not part of the C ABI).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "hicops.h"
+
+namespace hicops {
+
+// Physical constants (monoisotopic, Da).
+constexpr double kWaterDa = 18.010565;
+constexpr double kProtonDa = 1.007276466812;
+
+// Largest peptide length supported: modification state is a 64-bit mask.
+constexpr uint32_t kMaxLen = 64;
+constexpr uint32_t kHistBins = 256;
+constexpr uint32_t kMaxTopK = 32;
+constexpr uint32_t kMaxTopN = 1024;
+
+// Counter packing for one (spectrum, peptide) pair, 32 bits:
+//   bits 26..31 nb, bits 20..25 ny, bits 0..19 S (sum of quantised intensity).
+constexpr uint32_t kNbShift = 26;
+constexpr uint32_t kNyShift = 20;
+constexpr uint32_t kSMask = (1u << 20) - 1;
+
+// Thread-local error message (host.cpp).
+void set_error(const char* fmt, ...);
+
+// Host peptide table plus the device index.
+struct DeviceIndex {
+    bool ready = false;
+    int device = -1;
+    double* mass = nullptr;        // [P] neutral mass, pid order
+    uint64_t* off = nullptr;       // [n_bins + 1] bucket offsets
+    uint32_t* entry = nullptr;     // [E] pid << 1 | isY, pid ascending in a bucket
+    int64_t* lf = nullptr;         // [kMaxLen + 1] LF[n] = round(2^32 log10 n!)
+    int64_t* ls = nullptr;         // [s_max + 1]   LS[s] = round(2^32 log10 s)
+    uint64_t bytes = 0;
+    // optional per-phase timing of the last search (events on the call's stream)
+    bool timing = false;
+    void* ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+};
+
+// Counts every kernel launch of the library.
+void count_launches(uint64_t n);
+
+}  // namespace hicops
+
+struct hicops_index {
+    hicops_params p;
+    // residue masses used for every ion: unmodified (with fixed mod) and with
+    // the letter's variable modification, indexed by ASCII letter
+    double mres[128];
+    double mmod[128];
+    int8_t var_type[128];          // variable-mod rule per letter (-1 none)
+    uint32_t n_var = 0;
+    std::vector<double> var_delta;
+    std::vector<uint32_t> var_max;
+
+    // base (unmodified, deduplicated) peptides, in sequence-byte order
+    std::string residues;          // concatenated letters
+    std::vector<uint64_t> base_off;   // [B + 1]
+    // database entries in pid order
+    std::vector<double> mass;
+    std::vector<uint32_t> base;
+    std::vector<uint64_t> mask;
+
+    uint32_t n_bins = 0;           // bins 0 .. n_bins-1 (absolute bin numbers)
+    uint64_t s_max = 0;            // largest possible S
+    hicops_index_stats stats{};
+    hicops::DeviceIndex dev;
+};
+
+namespace hicops {
+hicops_status validate_params(const hicops_params* p);
+hicops_status upload_index(hicops_index* idx);
+void free_device_index(hicops_index* idx);
+}  // namespace hicops

@@ -1,0 +1,291 @@
+"""ctypes binding of ``libhicops.so`` (argument marshalling only).
+
+Every step of the search runs in the library's CUDA kernels; this module
+only converts arrays and tensors into pointers.  If the library has not been
+built, importing works but every call raises: there is no fallback path.
+PyTorch is used only for device memory and streams (``search_device``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EOVERFLOW, EBUSY, ECANCELLED = range(8)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ETIMEOUT", "EOVERFLOW", "EBUSY", "ECANCELLED"]
+MAX_PEAKS = 4096
+HIST_BINS = 256
+
+
+class HicopsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+class Mod(C.Structure):
+    _fields_ = [("residues", C.c_char_p), ("delta_da", C.c_double),
+                ("max_per_peptide", C.c_uint32), ("fixed", C.c_uint32)]
+
+
+class Params(C.Structure):
+    _fields_ = [("min_len", C.c_uint32), ("max_len", C.c_uint32), ("missed_cleavages", C.c_uint32),
+                ("max_total_mods", C.c_uint32), ("min_mass", C.c_double), ("max_mass", C.c_double),
+                ("frag_mz_min", C.c_double), ("frag_mz_max", C.c_double), ("bin_width_da", C.c_double),
+                ("top_n_peaks", C.c_uint32), ("min_shared", C.c_uint32), ("top_k", C.c_uint32),
+                ("hist_bins", C.c_uint32), ("intensity_scale", C.c_uint32), ("reserved", C.c_uint32)]
+
+
+class Proteins(C.Structure):
+    _fields_ = [("n_proteins", C.c_uint64), ("seq", C.c_void_p), ("off", C.c_void_p)]
+
+
+class Batch(C.Structure):
+    _fields_ = [("n", C.c_uint32), ("on_device", C.c_uint32), ("peak_off", C.c_void_p), ("mz", C.c_void_p),
+                ("intensity", C.c_void_p), ("prec_mz", C.c_void_p), ("charge", C.c_void_p),
+                ("prec_tol_da", C.c_void_p), ("cuda_stream", C.c_void_p)]
+
+
+class IndexStats(C.Structure):
+    _fields_ = [("n_peptides", C.c_uint64), ("n_base_peptides", C.c_uint64), ("n_entries", C.c_uint64),
+                ("n_bins", C.c_uint64), ("device_bytes", C.c_uint64), ("max_bucket", C.c_uint64),
+                ("host_ms", C.c_double), ("device_ms", C.c_double)]
+
+
+class Timing(C.Structure):
+    _fields_ = [("prep_ms", C.c_float), ("plan_ms", C.c_float), ("search_ms", C.c_float),
+                ("merge_ms", C.c_float), ("total_ms", C.c_float)]
+
+
+def kernel_launches() -> int:
+    return int(load().hicops_kernel_launches())
+
+
+PSM_DTYPE = np.dtype([("query", np.uint32), ("pid", np.uint32), ("nb", np.uint8), ("ny", np.uint8),
+                      ("reserved", np.uint16), ("hyperscore", np.float32), ("key", np.int64),
+                      ("evalue", np.float64)])
+assert PSM_DTYPE.itemsize == 32
+
+_lib = None
+EXPORTS = ["hicops_digest", "hicops_index_upload", "hicops_build_index", "hicops_search",
+           "hicops_search_work", "hicops_index_get_stats", "hicops_peptide", "hicops_index_copy_csr",
+           "hicops_index_free", "hicops_last_error"]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load the library (built in-tree by ``build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        if not build_if_missing:
+            raise RuntimeError(f"libhicops.so is not built ({_build.LIB}); run __graft_entry__.build()")
+        _build.build()
+    L = C.CDLL(_build.LIB)
+    P = C.c_void_p
+    st = C.c_int
+    sig = {
+        "hicops_digest": (st, [C.POINTER(Proteins), P, C.c_uint32, C.POINTER(Params), C.POINTER(P)]),
+        "hicops_index_upload": (st, [P]),
+        "hicops_build_index": (st, [C.POINTER(Proteins), P, C.c_uint32, C.POINTER(Params), C.POINTER(P)]),
+        "hicops_search": (st, [P, C.POINTER(Batch), P, P, P]),
+        "hicops_search_work": (st, [P, C.POINTER(Batch), P, P, P, P]),
+        "hicops_index_set_timing": (st, [P, C.c_int]),
+        "hicops_index_last_timing": (st, [P, C.POINTER(Timing)]),
+        "hicops_kernel_launches": (C.c_uint64, []),
+        "hicops_index_get_stats": (st, [P, C.POINTER(IndexStats)]),
+        "hicops_peptide": (st, [P, C.c_uint32, C.c_char_p, C.c_uint32, P, P]),
+        "hicops_index_copy_csr": (st, [P, P, P]),
+        "hicops_index_free": (None, [P]),
+        "hicops_last_error": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != OK:
+        raise HicopsError(status, load().hicops_last_error().decode(errors="replace"))
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def make_params(sp) -> Params:
+    return Params(min_len=sp.min_len, max_len=sp.max_len, missed_cleavages=sp.missed_cleavages,
+                  max_total_mods=sp.max_total_mods, min_mass=sp.min_mass, max_mass=sp.max_mass,
+                  frag_mz_min=sp.frag_mz_min, frag_mz_max=sp.frag_mz_max, bin_width_da=sp.bin_width_da,
+                  top_n_peaks=sp.top_n_peaks, min_shared=sp.min_shared, top_k=sp.top_k,
+                  hist_bins=sp.hist_bins, intensity_scale=sp.intensity_scale, reserved=0)
+
+
+@dataclass
+class SearchResult:
+    psm: np.ndarray       # PSM_DTYPE [n, top_k]
+    hist: np.ndarray      # uint32 [n, 256]
+    n_scored: np.ndarray  # uint32 [n]
+
+
+class Index:
+    """A database (superstep 1) and, once uploaded, its device fragment index."""
+
+    def __init__(self, seq: np.ndarray, off: np.ndarray, mods: Sequence, params, upload: bool = True):
+        L = load()
+        self.params = params
+        self.top_k = params.top_k
+        self._keep = [np.ascontiguousarray(seq, np.uint8), np.ascontiguousarray(off, np.uint64)]
+        arr = (Mod * max(1, len(mods)))()
+        self._mod_res = []
+        for i, m in enumerate(mods):
+            r = m.residues.encode()
+            self._mod_res.append(r)
+            arr[i] = Mod(r, m.delta_da, m.max_per_peptide, 1 if m.fixed else 0)
+        self._mods = arr
+        self._p = make_params(params)
+        prot = Proteins(len(self._keep[1]) - 1, _ptr(self._keep[0]).value, _ptr(self._keep[1]).value)
+        h = C.c_void_p()
+        _check(L.hicops_digest(C.byref(prot), C.cast(arr, C.c_void_p), len(mods), C.byref(self._p), C.byref(h)))
+        self.h = h
+        self._keep = None
+        if upload:
+            self.upload()
+
+    def upload(self):
+        _check(load().hicops_index_upload(self.h))
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value and _lib is not None:
+            _lib.hicops_index_free(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def stats(self) -> IndexStats:
+        s = IndexStats()
+        _check(load().hicops_index_get_stats(self.h, C.byref(s)))
+        return s
+
+    @property
+    def n_peptides(self) -> int:
+        return int(self.stats().n_peptides)
+
+    def peptide(self, pid: int):
+        buf = C.create_string_buffer(80)
+        mass = C.c_double()
+        mask = C.c_uint64()
+        _check(load().hicops_peptide(self.h, pid, buf, 80, C.byref(mass), C.byref(mask)))
+        return buf.value.decode(), mass.value, mask.value
+
+    def copy_csr(self):
+        st = self.stats()
+        off = np.zeros(st.n_bins + 1, np.uint64)
+        ent = np.zeros(max(1, st.n_entries), np.uint32)
+        _check(load().hicops_index_copy_csr(self.h, _ptr(off), _ptr(ent)))
+        return off, ent[:st.n_entries]
+
+    # ---- search through host buffers (the library copies in and out)
+
+    @staticmethod
+    def _host_batch(spec):
+        arrs = [np.ascontiguousarray(spec.peak_off, np.uint64), np.ascontiguousarray(spec.mz, np.float32),
+                np.ascontiguousarray(spec.intensity, np.float32), np.ascontiguousarray(spec.prec_mz, np.float64),
+                np.ascontiguousarray(spec.charge, np.uint8), np.ascontiguousarray(spec.tol_da, np.float64)]
+        b = Batch(len(arrs[3]), 0, *[_ptr(a).value for a in arrs], None)
+        return b, arrs
+
+    def search(self, spec) -> SearchResult:
+        b, keep = self._host_batch(spec)
+        n = b.n
+        psm = np.zeros((n, self.top_k), PSM_DTYPE)
+        hist = np.zeros((n, HIST_BINS), np.uint32)
+        ns = np.zeros(n, np.uint32)
+        _check(load().hicops_search(self.h, C.byref(b), _ptr(psm), _ptr(hist), _ptr(ns)))
+        return SearchResult(psm, hist, ns)
+
+    def search_work(self, spec):
+        """Per spectrum: window [lo, hi), retained peaks, index entries in the window (H)."""
+        b, keep = self._host_batch(spec)
+        n = b.n
+        lo = np.zeros(n, np.uint32)
+        hi = np.zeros(n, np.uint32)
+        npk = np.zeros(n, np.uint32)
+        hits = np.zeros(n, np.uint64)
+        _check(load().hicops_search_work(self.h, C.byref(b), _ptr(lo), _ptr(hi), _ptr(npk), _ptr(hits)))
+        return lo, hi, npk, hits
+
+    def set_timing(self, enable: bool = True):
+        _check(load().hicops_index_set_timing(self.h, 1 if enable else 0))
+
+    def last_timing(self) -> "Timing":
+        t = Timing()
+        _check(load().hicops_index_last_timing(self.h, C.byref(t)))
+        return t
+
+    # ---- search on device tensors (asynchronous on the given stream)
+
+    def search_device(self, dev_batch: "DeviceBatch", out: "DeviceResult", stream=None):
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        b = Batch(dev_batch.n, 1, dev_batch.peak_off.data_ptr(), dev_batch.mz.data_ptr(),
+                  dev_batch.intensity.data_ptr(), dev_batch.prec_mz.data_ptr(), dev_batch.charge.data_ptr(),
+                  dev_batch.tol_da.data_ptr(), s.cuda_stream)
+        _check(load().hicops_search(self.h, C.byref(b), out.psm.data_ptr(),
+                                    out.hist.data_ptr() if out.hist is not None else None,
+                                    out.n_scored.data_ptr() if out.n_scored is not None else None))
+
+
+@dataclass
+class DeviceBatch:
+    n: int
+    peak_off: "object"
+    mz: "object"
+    intensity: "object"
+    prec_mz: "object"
+    charge: "object"
+    tol_da: "object"
+
+    @classmethod
+    def from_spectra(cls, spec, device="cuda"):
+        import torch
+        t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dt)).to(device)   # noqa: E731
+        return cls(spec.n, t(spec.peak_off, np.uint64).view(torch.int64), t(spec.mz, np.float32),
+                   t(spec.intensity, np.float32), t(spec.prec_mz, np.float64), t(spec.charge, np.uint8),
+                   t(spec.tol_da, np.float64))
+
+
+@dataclass
+class DeviceResult:
+    psm: "object"        # uint8 tensor [n * top_k * 32]
+    hist: Optional["object"]
+    n_scored: Optional["object"]
+
+    @classmethod
+    def alloc(cls, n, top_k, device="cuda", hist=True):
+        import torch
+        return cls(torch.empty(n * top_k * PSM_DTYPE.itemsize, dtype=torch.uint8, device=device),
+                   torch.empty(n * HIST_BINS, dtype=torch.int32, device=device) if hist else None,
+                   torch.empty(n, dtype=torch.int32, device=device) if hist else None)
+
+    def to_host(self, n, top_k) -> SearchResult:
+        psm = self.psm.cpu().numpy().view(PSM_DTYPE).reshape(n, top_k)
+        hist = self.hist.cpu().numpy().view(np.uint32).reshape(n, HIST_BINS) if self.hist is not None else None
+        ns = self.n_scored.cpu().numpy().view(np.uint32) if self.n_scored is not None else None
+        return SearchResult(psm, hist, ns)

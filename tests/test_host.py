@@ -1,0 +1,111 @@
+"""Host-side checks (no GPU): the library loads and exports every entry point
+that include/*.h declares, parameter validation, and the host half of
+superstep 1 (digestion, variants, pid order) against the CPU oracle."""
+import ctypes as C
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2102_02286_gb300 import build as pkg_build
+from paper_2102_02286_gb300 import configs, synth
+from paper_2102_02286_gb300 import hicops as hc
+from paper_2102_02286_gb300.configs import SearchParams
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pkg_build.build()
+    return hc.load()
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(hicops_[A-Za-z0-9_]+)\s*\(",
+                             src, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert "hicops_search" in names and "hicops_build_index" in names
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in include/ but not exported"
+
+
+def test_param_validation(lib):
+    prot = synth.make_proteome(3, 1)
+    bad = [SearchParams(max_len=65), SearchParams(top_k=0), SearchParams(top_k=33), SearchParams(hist_bins=128),
+           SearchParams(bin_width_da=0.0), SearchParams(top_n_peaks=0), SearchParams(min_len=1),
+           SearchParams(intensity_scale=20000)]
+    for p in bad:
+        with pytest.raises(hc.HicopsError) as e:
+            hc.Index(prot.seq, prot.off, [], p, upload=False)
+        assert e.value.status in (hc.EINVAL, hc.EOVERFLOW)
+    # two variable rules on one residue are rejected
+    with pytest.raises(hc.HicopsError):
+        hc.Index(prot.seq, prot.off, [configs.OX_M(1), configs.Mod("M", 1.0, 1)], SearchParams(), upload=False)
+
+
+def test_search_without_device_index_is_rejected(lib):
+    prot = synth.make_proteome(3, 1)
+    idx = hc.Index(prot.seq, prot.off, [configs.CARBAMIDOMETHYL_C], SearchParams(), upload=False)
+    spec = synth.spectra_from_lists([([150.0, 250.0], [1.0, 2.0])], [500.0], [2], [10.0])
+    with pytest.raises(hc.HicopsError) as e:
+        idx.search(spec)
+    assert e.value.status == hc.EINVAL
+
+
+def _compare_tables(idx, db, mods):
+    var = [m for m in mods if not m.fixed]
+    n = db.n
+    assert idx.n_peptides == n
+    np.testing.assert_array_equal(db.masses(), np.array([idx.peptide(i)[1] for i in range(n)]))
+    for pid in range(n):
+        s, mass, mask = idx.peptide(pid)
+        os_, om, codes = db.peptide(pid)
+        assert s == os_
+        exp_mask = 0
+        for j, c in enumerate(codes):
+            if c:
+                assert s[j] in var[c - 1].residues
+                exp_mask |= 1 << j
+        assert mask == exp_mask
+
+
+def test_digest_matches_oracle_closed(lib, oracle_lib):
+    w = configs.TINY_CLOSED.with_proteins(150)
+    prot = synth.make_proteome(w.n_proteins, w.seed)
+    idx = hc.Index(prot.seq, prot.off, w.mods, w.params, upload=False)
+    db = oracle_lib.OracleDb(prot.seq, prot.off, w.mods, w.params)
+    _compare_tables(idx, db, w.mods)
+
+
+def test_digest_matches_oracle_modified(lib, oracle_lib):
+    w = configs.OPEN_LARGE.with_proteins(40)
+    prot = synth.make_proteome(w.n_proteins, w.seed)
+    idx = hc.Index(prot.seq, prot.off, w.mods, w.params, upload=False)
+    db = oracle_lib.OracleDb(prot.seq, prot.off, w.mods, w.params)
+    _compare_tables(idx, db, w.mods)
+    st = idx.stats()
+    assert st.n_base_peptides <= st.n_peptides
+
+
+def test_digest_global_cap_and_edges(lib, oracle_lib):
+    p = SearchParams(min_len=2, max_len=64, missed_cleavages=3, min_mass=0.0, max_mass=1e6, max_total_mods=2)
+    mods = [configs.CARBAMIDOMETHYL_C, configs.OX_M(3), configs.PHOSPHO_STY(2), configs.DEAMID_NQ(1)]
+    seqs = ["MSMSTYKCNQMSK", "AAXAAK", "PPPPKPPPR", "K", "R", "MMMMMMMMK", "C" * 63 + "K"]
+    s = "".join(seqs)
+    off = np.cumsum([0] + [len(x) for x in seqs]).astype(np.uint64)
+    arr = np.frombuffer(s.encode(), np.uint8)
+    idx = hc.Index(arr, off, mods, p, upload=False)
+    db = oracle_lib.OracleDb(arr, off, mods, p)
+    _compare_tables(idx, db, mods)
