@@ -291,7 +291,7 @@ def main():
     et = torch.tensor([sum(e2e_t)], dtype=torch.float64, device="cuda")
     if world > 1:
         dist.all_reduce(et, op=dist.ReduceOp.MAX)
-    e2e_value = world * n * len(e2e_t) / float(et.item())
+    e2e_value = world * n * len(e2e_t) / float(et.item()) if e2e_t else None
 
     peak, peak_src = measured_peaks()
     mean_search_s = statistics.mean(search_ms) / 1000.0

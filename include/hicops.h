@@ -193,6 +193,97 @@ hicops_status hicops_peptide(const hicops_index* index, uint32_t pid, char* seq,
  * offsets and entries [n_entries] = pid << 1 | isY.  Either may be NULL. */
 hicops_status hicops_index_copy_csr(const hicops_index* index, uint64_t* off, uint32_t* entries);
 
+/* Launch shape of the search kernel (the paper's R/I/K balancing of
+ * superstep 3 becomes the choice of how spectra and peptide ranges map onto
+ * persistent CTAs).  Zero fields take the default.  threads: CTA size, 256
+ * or 512.  chunk_mult: shared-memory counters per CTA = chunk_mult x 16384
+ * peptide ids, 1 or 2.  ctas_per_sm: resident CTAs per SM (0 = as many as
+ * fit).  seg_pids: a spectrum's precursor window is split into work units of
+ * at least this many peptide ids (0 = split only when the batch is too small
+ * to fill the GPU).  Results do not depend on the shape. */
+typedef struct hicops_search_config {
+    uint32_t threads;
+    uint32_t chunk_mult;
+    uint32_t ctas_per_sm;
+    uint32_t seg_pids;
+} hicops_search_config;
+
+/* Sets the launch shape hicops_search uses for this index (NULL = defaults).
+ * Errors: HICOPS_EINVAL for an unsupported shape. */
+hicops_status hicops_index_set_config(hicops_index* index, const hicops_search_config* cfg);
+
+/* Times every candidate launch shape on a device-resident sample batch
+ * (on_device = 1) and stores the fastest in the index (as
+ * hicops_index_set_config would); *best and *best_ms receive it when not
+ * NULL.  Synchronises the batch's stream. */
+hicops_status hicops_autotune(hicops_index* index, const hicops_batch* sample, hicops_search_config* best,
+                              double* best_ms);
+
+/* A reusable search (the batched form): device scratch for up to
+ * max_spectra spectra is allocated once at creation, and hicops_plan_search
+ * enqueues the whole search (preprocessing to e-value) on the batch's stream
+ * without allocating.  With use_graph = 1 and a non-NULL stream, the first
+ * call for a given (batch, outputs) is captured into a CUDA graph and later
+ * calls with the same pointers and sizes replay it.  The batch and outputs
+ * must be device pointers (on_device = 1).  A plan serves one stream at a
+ * time.  Errors: HICOPS_EINVAL (batch larger than max_spectra, host
+ * pointers), HICOPS_ENOMEM, HICOPS_ECUDA. */
+typedef struct hicops_plan hicops_plan;
+hicops_status hicops_plan_create(hicops_index* index, uint32_t max_spectra, const hicops_search_config* cfg,
+                                 hicops_plan** out);
+hicops_status hicops_plan_search(hicops_plan* plan, const hicops_batch* batch, hicops_psm* out_psm,
+                                 uint32_t* out_hist, uint32_t* out_nscored, int use_graph);
+void hicops_plan_destroy(hicops_plan* plan);
+
+/* Serving loop (the paper's buffering and R/I/K pipeline of superstep 3,
+ * Buffering and Task Scheduling sections, as a request server).  The index
+ * stays resident; requests (batches of spectra in host memory) are copied at
+ * submission and queued; a scheduler thread packs waiting requests into the
+ * next launch on one of n_slots streams as soon as a slot is free, so
+ * requests that arrive while others run are admitted as slots free up and
+ * their work overlaps on the device.  Each slot owns a reusable plan for up
+ * to slot_spectra spectra; slots are created while their scratch fits in
+ * memory_budget bytes.  A request of more than slot_spectra spectra is
+ * rejected (HICOPS_EINVAL).  Results do not depend on how requests are
+ * packed.  Zero fields take the defaults (4 slots, 16 GiB, 32768 spectra). */
+typedef struct hicops_server_cfg {
+    uint32_t n_slots;
+    uint32_t slot_spectra;
+    uint64_t memory_budget;
+} hicops_server_cfg;
+
+typedef struct hicops_server_stats {
+    uint64_t submitted, completed, launches, spectra;
+    uint32_t n_slots;          /* slots actually created within the budget */
+    uint32_t reserved;
+    uint64_t slot_bytes;       /* device scratch per slot */
+} hicops_server_stats;
+
+typedef struct hicops_server hicops_server;
+
+hicops_status hicops_server_create(hicops_index* index, const hicops_server_cfg* cfg, hicops_server** out);
+
+/* Queues a request (batch in host memory, on_device = 0; the arrays are
+ * copied before the call returns).  *ticket identifies it for poll/cancel. */
+hicops_status hicops_server_submit(hicops_server* srv, const hicops_batch* batch, uint64_t* ticket);
+
+/* Waits up to timeout_ms (0 = do not wait, < 0 = wait forever) for the
+ * request; when it is done, copies its rows [n * top_k], histograms
+ * [n * 256] and candidate counts [n] (either may be NULL) to host memory
+ * and forgets the ticket.  HICOPS_ETIMEOUT: not done yet (the ticket stays
+ * valid); HICOPS_ECANCELLED: cancelled; HICOPS_EINVAL: unknown ticket. */
+hicops_status hicops_server_poll(hicops_server* srv, uint64_t ticket, int timeout_ms, hicops_psm* out_psm,
+                                 uint32_t* out_hist, uint32_t* out_nscored);
+
+/* Cancels a request that has not been launched yet (HICOPS_EBUSY if it
+ * has). */
+hicops_status hicops_server_cancel(hicops_server* srv, uint64_t ticket);
+
+hicops_status hicops_server_get_stats(hicops_server* srv, hicops_server_stats* out);
+
+/* Waits for launched work, drops queued requests, frees the slots. */
+void hicops_server_destroy(hicops_server* srv);
+
 /* Per-phase device time of the last hicops_search on this index, measured
  * with CUDA events recorded on the call's stream.  Measurement only: with
  * timing enabled, concurrent searches on one index overwrite each other's

@@ -19,6 +19,14 @@ constexpr uint32_t kHistBins = 256;
 constexpr uint32_t kMaxTopK = 32;
 constexpr uint32_t kMaxTopN = 1024;
 
+// The search walks peptide ids in chunks of 2^kChunkShift; every bucket
+// stores where each chunk starts (the skip table).
+constexpr uint32_t kChunkShift = 14;
+constexpr uint32_t kChunk = 1u << kChunkShift;
+// A bucket holding at least P >> kHotShift entries (1/32 of the database)
+// is also stored as a pid bitmap.
+constexpr uint32_t kHotShift = 5;
+
 // Counter packing for one (spectrum, peptide) pair, 32 bits:
 //   bits 26..31 nb, bits 20..25 ny, bits 0..19 S (sum of quantised intensity).
 constexpr uint32_t kNbShift = 26;
@@ -37,10 +45,24 @@ struct DeviceIndex {
     uint32_t* entry = nullptr;     // [E] pid << 1 | isY, pid ascending in a bucket
     int64_t* lf = nullptr;         // [kMaxLen + 1] LF[n] = round(2^32 log10 n!)
     int64_t* ls = nullptr;         // [s_max + 1]   LS[s] = round(2^32 log10 s)
+    // chunk skip table of every non-empty bucket: row[bin] (-1 empty) and
+    // skip[row * skip_stride + j] = entries with pid < j << kChunkShift
+    int32_t* skip_row = nullptr;   // [n_bins]
+    uint32_t* skip = nullptr;      // [rows * skip_stride]
+    uint32_t skip_stride = 0;      // chunks + 1
+    // hot buckets (at least P >> kHotShift entries) as pid bitmaps
+    int32_t* hot_id = nullptr;     // [n_bins] (-1 not hot)
+    uint32_t* hot_b = nullptr;     // [n_hot * hot_words] b-ion bits
+    uint32_t* hot_y = nullptr;     // [n_hot * hot_words] y-ion bits
+    uint32_t* hot_flags = nullptr; // [n_hot] bit 0: has b entries, bit 1: has y entries
+    uint32_t n_hot = 0;
+    uint64_t hot_words = 0;
     uint64_t bytes = 0;
     // optional per-phase timing of the last search (events on the call's stream)
     bool timing = false;
     void* ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    // launch shape used by hicops_search
+    hicops_search_config cfg = {0, 0, 0, 0};
 };
 
 // Counts every kernel launch of the library.

@@ -5,6 +5,7 @@
 // CFIR-style inverted index built by a parallel sort; here the sort is a
 // stable LSD radix sort by bin over (bin, pid, isY) keys emitted in pid
 // order, so each bucket comes out pid-ascending without a comparison sort.
+#include <algorithm>
 #include <cmath>
 #include <chrono>
 #include <vector>
@@ -211,6 +212,52 @@ __global__ void bucket_max_kernel(const uint64_t* __restrict__ off, uint32_t nbi
     if (b < nbins) atomicMax(mx, (unsigned long long)(off[b + 1] - off[b]));
 }
 
+// flag[b] = bucket b holds at least lo entries (and is hot when lo > 1)
+__global__ void bucket_flag_kernel(const uint64_t* __restrict__ off, uint32_t nbins, uint64_t lo,
+                                   uint32_t* __restrict__ flag) {
+    const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nbins) flag[b] = (off[b + 1] - off[b]) >= lo ? 1u : 0u;
+}
+
+__global__ void row_of_kernel(const uint32_t* __restrict__ flag, const uint64_t* __restrict__ scan, uint32_t nbins,
+                              int32_t* __restrict__ row) {
+    const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nbins) row[b] = flag[b] ? (int32_t)scan[b] : -1;
+}
+
+// Chunk skip table: skip[row * stride + j] = number of entries of the bucket
+// with pid < j * 2^kChunkShift, for j = 0 .. stride-1 (the last column is the
+// bucket size).  Every cell is written by exactly one entry.
+__global__ void skip_fill_kernel(const uint64_t* __restrict__ keys, uint64_t n, const uint64_t* __restrict__ off,
+                                 const int32_t* __restrict__ row, uint32_t stride, uint32_t* __restrict__ skip) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t bin = (uint32_t)(keys[i] >> 32);
+    const uint32_t ch = ((uint32_t)keys[i] >> 1) >> kChunkShift;
+    const uint64_t b0 = off[bin], b1 = off[bin + 1];
+    uint32_t* base = skip + (uint64_t)row[bin] * stride;
+    const uint32_t rel = (uint32_t)(i - b0);
+    const uint32_t jlo = (i == b0) ? 0u : (((uint32_t)keys[i - 1] >> 1) >> kChunkShift) + 1u;
+    for (uint32_t j = jlo; j <= ch; ++j) base[j] = rel;
+    if (i + 1 == b1)
+        for (uint32_t j = ch + 1; j < stride; ++j) base[j] = (uint32_t)(b1 - b0);
+}
+
+// Hot buckets as pid bitmaps: bit pid of hb[h] (b ion) or hy[h] (y ion).
+__global__ void hot_fill_kernel(const uint64_t* __restrict__ keys, uint64_t n, const int32_t* __restrict__ hot_id,
+                                uint64_t words, uint32_t* __restrict__ hb, uint32_t* __restrict__ hy,
+                                uint32_t* __restrict__ hflags) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t h = hot_id[(uint32_t)(keys[i] >> 32)];
+    if (h < 0) return;
+    const uint32_t e = (uint32_t)keys[i];
+    const uint32_t pid = e >> 1;
+    uint32_t* bm = (e & 1u) ? hy : hb;
+    atomicOr(&bm[(uint64_t)h * words + (pid >> 5)], 1u << (pid & 31));
+    atomicOr(&hflags[h], (e & 1u) ? 2u : 1u);
+}
+
 template <class T>
 cudaError_t dalloc(T** p, uint64_t n, std::vector<void*>& tmp) {
     cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (n ? n : 1));
@@ -236,6 +283,12 @@ void free_device_index(hicops_index* idx) {
         cudaFree(d.entry);
         cudaFree(d.lf);
         cudaFree(d.ls);
+        cudaFree(d.skip_row);
+        cudaFree(d.skip);
+        cudaFree(d.hot_id);
+        cudaFree(d.hot_b);
+        cudaFree(d.hot_y);
+        cudaFree(d.hot_flags);
         for (void* e : d.ev) if (e) cudaEventDestroy((cudaEvent_t)e);
         if (cur >= 0 && cur != d.device) cudaSetDevice(cur);
     }
@@ -350,8 +403,58 @@ hicops_status upload_index(hicops_index* idx) {
         set_error("a bucket holds %llu entries (limit 2^32)", (unsigned long long)mx);
         return HICOPS_EOVERFLOW;
     }
+
+    // chunk skip tables for every non-empty bucket
+    const uint32_t nb = idx->n_bins;
+    const unsigned bgrid = (nb + 255) / 256;
+    const unsigned egrid = (unsigned)((E + 255) / 256);
+    uint32_t* flag;
+    uint64_t *rscan, *rtotal, *btmp;
+    HC_CUDA(dalloc(&flag, nb, tf.ptrs));
+    HC_CUDA(dalloc(&rscan, nb, tf.ptrs));
+    HC_CUDA(dalloc(&rtotal, 1, tf.ptrs));
+    HC_CUDA(dalloc(&btmp, scan_tmp_words(nb), tf.ptrs));
+    bucket_flag_kernel<<<bgrid, 256, 0, s>>>(d.off, nb, 1, flag);
+    HC_CUDA(cudaGetLastError());
+    HC_CUDA(exclusive_scan<uint32_t>(flag, nb, rscan, rtotal, btmp, s));
+    HC_CUDA(cudaMalloc(&d.skip_row, sizeof(int32_t) * nb));
+    row_of_kernel<<<bgrid, 256, 0, s>>>(flag, rscan, nb, d.skip_row);
+    HC_CUDA(cudaGetLastError());
+    uint64_t rows = 0;
+    HC_CUDA(cudaMemcpyAsync(&rows, rtotal, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    HC_CUDA(cudaStreamSynchronize(s));
+    d.skip_stride = (uint32_t)(((P + kChunk - 1) >> kChunkShift) + 1);
+    HC_CUDA(cudaMalloc(&d.skip, sizeof(uint32_t) * (rows ? rows : 1) * d.skip_stride));
+    if (E) skip_fill_kernel<<<egrid, 256, 0, s>>>(keys, E, d.off, d.skip_row, d.skip_stride, d.skip);
+    HC_CUDA(cudaGetLastError());
+
+    // hot buckets as bitmaps
+    const uint64_t hot_lo = std::max<uint64_t>(2, P >> kHotShift);
+    bucket_flag_kernel<<<bgrid, 256, 0, s>>>(d.off, nb, hot_lo, flag);
+    HC_CUDA(cudaGetLastError());
+    HC_CUDA(exclusive_scan<uint32_t>(flag, nb, rscan, rtotal, btmp, s));
+    HC_CUDA(cudaMalloc(&d.hot_id, sizeof(int32_t) * nb));
+    row_of_kernel<<<bgrid, 256, 0, s>>>(flag, rscan, nb, d.hot_id);
+    HC_CUDA(cudaGetLastError());
+    uint64_t nhot = 0;
+    HC_CUDA(cudaMemcpyAsync(&nhot, rtotal, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    HC_CUDA(cudaStreamSynchronize(s));
+    d.n_hot = (uint32_t)nhot;
+    d.hot_words = (P + 31) / 32 + 1;
+    const uint64_t hbytes = sizeof(uint32_t) * (nhot ? nhot : 1) * d.hot_words;
+    HC_CUDA(cudaMalloc(&d.hot_b, hbytes));
+    HC_CUDA(cudaMalloc(&d.hot_y, hbytes));
+    HC_CUDA(cudaMalloc(&d.hot_flags, sizeof(uint32_t) * (nhot ? nhot : 1)));
+    HC_CUDA(cudaMemsetAsync(d.hot_b, 0, hbytes, s));
+    HC_CUDA(cudaMemsetAsync(d.hot_y, 0, hbytes, s));
+    HC_CUDA(cudaMemsetAsync(d.hot_flags, 0, sizeof(uint32_t) * (nhot ? nhot : 1), s));
+    if (E && nhot) hot_fill_kernel<<<egrid, 256, 0, s>>>(keys, E, d.hot_id, d.hot_words, d.hot_b, d.hot_y, d.hot_flags);
+    HC_CUDA(cudaGetLastError());
+    HC_CUDA(cudaStreamSynchronize(s));
+
     d.bytes = sizeof(double) * P + sizeof(uint64_t) * (idx->n_bins + 1) + sizeof(uint32_t) * E +
-              sizeof(int64_t) * (lf.size() + ls.size());
+              sizeof(int64_t) * (lf.size() + ls.size()) + sizeof(int32_t) * 2 * nb +
+              sizeof(uint32_t) * rows * d.skip_stride + 2 * hbytes;
     idx->stats.n_entries = E;
     idx->stats.max_bucket = mx;
     idx->stats.device_bytes = d.bytes;

@@ -1,0 +1,348 @@
+// Device kernels of the search path (included by search.cu only):
+// preprocessing + precursor window, unit planning, the shared-peak search
+// kernel (search_kernel.cuh), the top-k merge + e-value, and the work count.
+#pragma once
+
+#include <cfloat>
+#include <cmath>
+
+#include "dev_common.cuh"
+
+namespace hicops {
+namespace {
+
+constexpr int kPrepThreads = 256;
+constexpr int kSearchThreads = 256;
+constexpr int kMinSegPids = (int)kChunk;  // smallest segment of a split window
+constexpr int kMaxSegs = 64;              // most segments a window is split into
+constexpr int kMergeThreads = 256;
+constexpr uint16_t kNoIdx = 0xffff;       // padding slot of the merge sort
+
+struct UnitTop {
+    int64_t key;
+    uint32_t pid;
+    uint32_t packed;    // nb << 26 | ny << 20 | S
+};
+
+struct PrepArgs {
+    const uint64_t* peak_off;
+    const float* mz;
+    const float* inten;
+    const double* prec_mz;
+    const uint8_t* charge;
+    const double* tol;
+    uint32_t n;
+    uint32_t topn;
+    double w, mz_lo, mz_hi, scale;
+    const double* mass;
+    uint64_t P;
+    uint32_t* qbin;     // [n * topn]
+    uint32_t* qiq;      // [n * topn]
+    uint32_t* qn;       // [n]
+    uint32_t* lo;       // [n]
+    uint32_t* hi;       // [n]
+};
+
+__device__ __forceinline__ void bitonic_sort_u64(uint64_t* s, int npow) {
+    for (int k = 2; k <= npow; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < npow; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const uint64_t a = s[i], b = s[ixj];
+                    const bool up = (i & k) == 0;
+                    if ((a > b) == up) { s[i] = b; s[ixj] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__device__ __forceinline__ int next_pow2(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+// first index in [0, n) with mass[i] >= x  (or > x when upper)
+__device__ __forceinline__ uint64_t mass_bound(const double* mass, uint64_t n, double x, bool upper) {
+    uint64_t a = 0, b = n;
+    while (a < b) {
+        const uint64_t m = (a + b) >> 1;
+        const double v = mass[m];
+        if (upper ? (v <= x) : (v < x)) a = m + 1; else b = m;
+    }
+    return a;
+}
+
+__global__ void __launch_bounds__(kPrepThreads) prep_kernel(PrepArgs a) {
+    __shared__ uint64_t keys[HICOPS_MAX_PEAKS];
+    __shared__ int s_nrep;
+    const uint32_t q = blockIdx.x;
+    const uint64_t p0 = a.peak_off[q], p1 = a.peak_off[q + 1];
+    const uint64_t cnt = p1 >= p0 ? p1 - p0 : 0;
+    const double prec = a.prec_mz[q];
+    const double tol = a.tol[q];
+    const uint32_t z = a.charge[q];
+    bool valid = cnt <= HICOPS_MAX_PEAKS && p1 >= p0 && z > 0 && isfinite(prec) && isfinite(tol) && tol >= 0.0;
+    int keep = 0;
+    if (valid && cnt > 0) {
+        const int npow = next_pow2((int)cnt);
+        // key = bin << 32 | intensity bits (positive finite floats order as integers)
+        for (int i = threadIdx.x; i < npow; i += blockDim.x) {
+            uint64_t k = ~0ull;
+            if (i < (int)cnt) {
+                const float m = a.mz[p0 + i], I = a.inten[p0 + i];
+                const double md = (double)m;
+                if (isfinite(m) && isfinite(I) && I > 0.0f && md >= a.mz_lo && md < a.mz_hi) {
+                    const uint32_t bin = (uint32_t)floor(md / a.w);
+                    k = ((uint64_t)bin << 32) | __float_as_uint(I);
+                }
+            }
+            keys[i] = k;
+        }
+        if (threadIdx.x == 0) s_nrep = 0;
+        __syncthreads();
+        bitonic_sort_u64(keys, npow);
+        // one representative per bin: the last (most intense) of each run
+        uint64_t rep[HICOPS_MAX_PEAKS / kPrepThreads];
+        int nr = 0;
+        for (int i = threadIdx.x; i < npow; i += blockDim.x) {
+            const uint64_t k = keys[i];
+            if (k == ~0ull) continue;
+            const bool last = (i + 1 == npow) || ((keys[i + 1] >> 32) != (k >> 32));
+            // re-key: intensity descending, then bin ascending
+            if (last) rep[nr++] = ((uint64_t)(~(uint32_t)k) << 32) | (k >> 32);
+        }
+        __syncthreads();
+        for (int r = 0; r < nr; ++r) keys[atomicAdd(&s_nrep, 1)] = rep[r];
+        __syncthreads();
+        const int nrep = s_nrep;
+        const int npow2 = next_pow2(nrep > 0 ? nrep : 1);
+        for (int i = nrep + threadIdx.x; i < npow2; i += blockDim.x) keys[i] = ~0ull;
+        __syncthreads();
+        bitonic_sort_u64(keys, npow2);
+        keep = nrep < (int)a.topn ? nrep : (int)a.topn;
+        if (keep > 0) {
+            const double Imax = (double)__uint_as_float(~(uint32_t)(keys[0] >> 32));
+            for (int t = threadIdx.x; t < keep; t += blockDim.x) {
+                const uint64_t k = keys[t];
+                const double I = (double)__uint_as_float(~(uint32_t)(k >> 32));
+                const double r = floor(__dmul_rn(I, a.scale) / Imax);
+                a.qbin[(uint64_t)q * a.topn + t] = (uint32_t)k;
+                a.qiq[(uint64_t)q * a.topn + t] = r < 1.0 ? 1u : (uint32_t)r;
+            }
+        }
+    }
+    valid = valid && keep > 0;
+    if (threadIdx.x == 0) {
+        a.qn[q] = valid ? (uint32_t)keep : 0u;
+        uint32_t lo = 0, hi = 0;
+        if (valid) {
+            const double Mq = __dmul_rn(__dsub_rn(prec, kProtonDa), (double)z);
+            lo = (uint32_t)mass_bound(a.mass, a.P, __dsub_rn(Mq, tol), false);
+            hi = (uint32_t)mass_bound(a.mass, a.P, __dadd_rn(Mq, tol), true);
+        }
+        a.lo[q] = lo;
+        a.hi[q] = hi;
+    }
+}
+
+// work units per spectrum: its window split into pieces of >= seg_pids ids
+__global__ void plan_kernel(const uint32_t* __restrict__ qn, const uint32_t* __restrict__ lo,
+                            const uint32_t* __restrict__ hi, uint32_t n, uint32_t max_seg, uint32_t seg_pids,
+                            uint32_t* __restrict__ nseg) {
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    uint32_t s = 0;
+    if (qn[q] > 0 && hi[q] > lo[q]) {
+        const uint32_t W = hi[q] - lo[q];
+        s = (uint32_t)(((uint64_t)W + seg_pids - 1) / seg_pids);
+        if (s > max_seg) s = max_seg;
+    }
+    nseg[q] = s;
+}
+
+#include "search_kernel.cuh"
+
+// lower bound of pid key (pid << 1) in entry[a, b)
+__device__ __forceinline__ uint64_t entry_lower_bound(const uint32_t* __restrict__ entry, uint64_t a, uint64_t b,
+                                                      uint32_t pid) {
+    const uint32_t key = pid << 1;
+    while (a < b) {
+        const uint64_t m = (a + b) >> 1;
+        if (__ldg(entry + m) < key) a = m + 1; else b = m;
+    }
+    return a;
+}
+
+struct MergeArgs {
+    const uint64_t* seg_off;
+    const UnitTop* utop;
+    const uint32_t* hist;
+    uint32_t n, k;
+    uint32_t q_base;          // query index written into the rows
+    hicops_psm* out;
+};
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double t = 0;
+    for (int i = 0; i < (int)(blockDim.x / 32); ++i) t += red[i];
+    return t;
+}
+
+// one block per spectrum: merge the segment lists, then the e-value fit
+__global__ void __launch_bounds__(kMergeThreads) merge_kernel(MergeArgs a) {
+    __shared__ UnitTop buf[kMaxSegs * kMaxTopK];
+    __shared__ uint16_t sk[kMaxSegs * kMaxTopK];
+    __shared__ uint32_t suf[kHistBins];
+    __shared__ double red[kMergeThreads / 32];
+    __shared__ uint32_t s_mode;
+    const uint32_t q = blockIdx.x;
+    const uint32_t k = a.k;
+    const uint64_t u0 = a.seg_off[q], u1 = a.seg_off[q + 1];
+    const int nseg = (int)(u1 - u0);
+    const int m = nseg * (int)k;
+    // sort (key desc, pid asc) by sorting an index-tagged 64-bit rank
+    const int npow = next_pow2(m > 0 ? m : 1);
+    for (int i = threadIdx.x; i < npow; i += blockDim.x) {
+        if (i < m) {
+            buf[i] = a.utop[u0 * k + i];
+            sk[i] = (uint16_t)i;
+        } else {
+            sk[i] = kNoIdx;
+        }
+    }
+    __syncthreads();
+    // odd-even by comparator over buf via index sort (bitonic on indices)
+    for (int kk = 2; kk <= npow; kk <<= 1) {
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < npow; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const uint16_t x = sk[i], y = sk[ixj];
+                    // "x after y" in (key desc, pid asc) order; padding last
+                    bool x_after;
+                    if (x == kNoIdx) x_after = (y != kNoIdx);
+                    else if (y == kNoIdx) x_after = false;
+                    else x_after = better(buf[y].key, buf[y].pid, buf[x].key, buf[x].pid);
+                    const bool up = (i & kk) == 0;
+                    if (x_after == up) { sk[i] = y; sk[ixj] = x; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // survival function and fit over the histogram
+    const uint32_t* h = a.hist + (uint64_t)q * kHistBins;
+    const int j = threadIdx.x;   // one bin per thread (256 threads)
+    const uint32_t hv = h[j];
+    // suffix sums
+    suf[j] = hv;
+    __syncthreads();
+    for (int o = 1; o < (int)kHistBins; o <<= 1) {
+        const uint32_t add = (j + o < (int)kHistBins) ? suf[j + o] : 0u;
+        __syncthreads();
+        suf[j] += add;
+        __syncthreads();
+    }
+    // mode: highest count, lowest bin on ties
+    if (j == 0) s_mode = 0;
+    __syncthreads();
+    {
+        const uint64_t v = ((uint64_t)hv << 32) | (uint32_t)(255 - j);
+        uint64_t best = v;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const uint64_t ov = __shfl_xor_sync(0xffffffffu, best, o);
+            if (ov > best) best = ov;
+        }
+        __shared__ uint64_t wbest[kMergeThreads / 32];
+        if ((j & 31) == 0) wbest[j >> 5] = best;
+        __syncthreads();
+        if (j == 0) {
+            uint64_t b = wbest[0];
+            for (int w = 1; w < kMergeThreads / 32; ++w) if (wbest[w] > b) b = wbest[w];
+            s_mode = 255 - (uint32_t)(b & 0xffffffffu);
+        }
+        __syncthreads();
+    }
+    const double N = (double)suf[0];
+    const bool have_top = m > 0 && sk[0] != kNoIdx && buf[sk[0]].pid != 0xffffffffu;
+    int64_t jtop = 0;
+    if (have_top) { jtop = buf[sk[0]].key >> 31; if (jtop > 255) jtop = 255; }
+    const bool pt = have_top && j >= (int)s_mode + 1 && j <= jtop - 1 && suf[j] > 0;
+    const double x = (double)j;
+    const double y = pt ? log10((double)suf[j] / N) : 0.0;
+    const double cn = block_sum(pt ? 1.0 : 0.0, red);
+    const double sx = block_sum(pt ? x : 0.0, red);
+    const double sy = block_sum(pt ? y : 0.0, red);
+    const double sxx = block_sum(pt ? x * x : 0.0, red);
+    const double sxy = block_sum(pt ? x * y : 0.0, red);
+    const bool fit = cn >= 3.0;
+    double wfit = 0.0, bfit = 0.0;
+    if (fit) {
+        const double den = cn * sxx - sx * sx;
+        wfit = (cn * sxy - sx * sy) / den;
+        bfit = (sy - wfit * sx) / cn;
+    }
+    for (uint32_t r = threadIdx.x; r < k; r += blockDim.x) {
+        hicops_psm o;
+        o.query = a.q_base + q;
+        o.reserved = 0;
+        const bool real = (int)r < m && sk[r] != kNoIdx && buf[sk[r]].pid != 0xffffffffu;
+        if (real) {
+            const UnitTop t = buf[sk[r]];
+            o.pid = t.pid;
+            o.nb = (uint8_t)(t.packed >> kNbShift);
+            o.ny = (uint8_t)((t.packed >> kNyShift) & 63u);
+            o.key = t.key;
+            o.hyperscore = (float)((double)t.key * 0x1p-32);
+            if (fit) o.evalue = N * exp10(wfit * ((double)t.key * 0x1p-31) + bfit);
+            else o.evalue = N;
+        } else {
+            o.pid = 0xffffffffu;
+            o.nb = o.ny = 0;
+            o.key = INT64_MIN;
+            o.hyperscore = 0.0f;
+            o.evalue = INFINITY;
+        }
+        a.out[(uint64_t)q * k + r] = o;
+    }
+}
+
+// per spectrum: sum over retained peaks of the bucket entries inside [lo, hi)
+__global__ void work_kernel(const uint32_t* __restrict__ qbin, const uint32_t* __restrict__ qn,
+                            const uint32_t* __restrict__ lo, const uint32_t* __restrict__ hi, uint32_t topn,
+                            const uint64_t* __restrict__ off, const uint32_t* __restrict__ entry,
+                            uint64_t* __restrict__ hits) {
+    const uint32_t q = blockIdx.x;
+    uint64_t h = 0;
+    for (uint32_t t = threadIdx.x; t < qn[q]; t += blockDim.x) {
+        const uint32_t bin = qbin[(uint64_t)q * topn + t];
+        const uint64_t b0 = off[bin], b1 = off[bin + 1];
+        const uint64_t c = entry_lower_bound(entry, b0, b1, lo[q]);
+        const uint64_t e = entry_lower_bound(entry, c, b1, hi[q]);
+        h += e - c;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
+    __shared__ uint64_t red[8];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = h;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint64_t t = 0;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += red[w];
+        hits[q] = t;
+    }
+}
+
+}  // namespace
+}  // namespace hicops

@@ -57,6 +57,24 @@ class IndexStats(C.Structure):
                 ("host_ms", C.c_double), ("device_ms", C.c_double)]
 
 
+class SearchConfig(C.Structure):
+    _fields_ = [("threads", C.c_uint32), ("chunk_mult", C.c_uint32), ("ctas_per_sm", C.c_uint32),
+                ("seg_pids", C.c_uint32)]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+class ServerCfg(C.Structure):
+    _fields_ = [("n_slots", C.c_uint32), ("slot_spectra", C.c_uint32), ("memory_budget", C.c_uint64)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("launches", C.c_uint64),
+                ("spectra", C.c_uint64), ("n_slots", C.c_uint32), ("reserved", C.c_uint32),
+                ("slot_bytes", C.c_uint64)]
+
+
 class Timing(C.Structure):
     _fields_ = [("prep_ms", C.c_float), ("plan_ms", C.c_float), ("search_ms", C.c_float),
                 ("merge_ms", C.c_float), ("total_ms", C.c_float)]
@@ -99,6 +117,17 @@ def load(build_if_missing: bool = False):
         "hicops_build_index": (st, [C.POINTER(Proteins), P, C.c_uint32, C.POINTER(Params), C.POINTER(P)]),
         "hicops_search": (st, [P, C.POINTER(Batch), P, P, P]),
         "hicops_search_work": (st, [P, C.POINTER(Batch), P, P, P, P]),
+        "hicops_index_set_config": (st, [P, C.POINTER(SearchConfig)]),
+        "hicops_autotune": (st, [P, C.POINTER(Batch), C.POINTER(SearchConfig), C.POINTER(C.c_double)]),
+        "hicops_plan_create": (st, [P, C.c_uint32, C.POINTER(SearchConfig), C.POINTER(P)]),
+        "hicops_plan_search": (st, [P, C.POINTER(Batch), P, P, P, C.c_int]),
+        "hicops_plan_destroy": (None, [P]),
+        "hicops_server_create": (st, [P, C.POINTER(ServerCfg), C.POINTER(P)]),
+        "hicops_server_submit": (st, [P, C.POINTER(Batch), C.POINTER(C.c_uint64)]),
+        "hicops_server_poll": (st, [P, C.c_uint64, C.c_int, P, P, P]),
+        "hicops_server_cancel": (st, [P, C.c_uint64]),
+        "hicops_server_get_stats": (st, [P, C.POINTER(ServerStats)]),
+        "hicops_server_destroy": (None, [P]),
         "hicops_index_set_timing": (st, [P, C.c_int]),
         "hicops_index_last_timing": (st, [P, C.POINTER(Timing)]),
         "hicops_kernel_launches": (C.c_uint64, []),
@@ -231,6 +260,20 @@ class Index:
         _check(load().hicops_search_work(self.h, C.byref(b), _ptr(lo), _ptr(hi), _ptr(npk), _ptr(hits)))
         return lo, hi, npk, hits
 
+    def set_config(self, cfg: Optional[SearchConfig] = None):
+        _check(load().hicops_index_set_config(self.h, C.byref(cfg) if cfg is not None else None))
+
+    def autotune(self, dev_batch: "DeviceBatch", stream=None):
+        """Times the candidate launch shapes on a device batch; keeps the fastest."""
+        b = _device_batch_struct(dev_batch, stream)
+        best = SearchConfig()
+        ms = C.c_double()
+        _check(load().hicops_autotune(self.h, C.byref(b), C.byref(best), C.byref(ms)))
+        return best, ms.value
+
+    def plan(self, max_spectra: int, cfg: Optional[SearchConfig] = None) -> "Plan":
+        return Plan(self, max_spectra, cfg)
+
     def set_timing(self, enable: bool = True):
         _check(load().hicops_index_set_timing(self.h, 1 if enable else 0))
 
@@ -242,14 +285,47 @@ class Index:
     # ---- search on device tensors (asynchronous on the given stream)
 
     def search_device(self, dev_batch: "DeviceBatch", out: "DeviceResult", stream=None):
-        import torch
-        s = stream if stream is not None else torch.cuda.current_stream()
-        b = Batch(dev_batch.n, 1, dev_batch.peak_off.data_ptr(), dev_batch.mz.data_ptr(),
-                  dev_batch.intensity.data_ptr(), dev_batch.prec_mz.data_ptr(), dev_batch.charge.data_ptr(),
-                  dev_batch.tol_da.data_ptr(), s.cuda_stream)
+        b = _device_batch_struct(dev_batch, stream)
         _check(load().hicops_search(self.h, C.byref(b), out.psm.data_ptr(),
                                     out.hist.data_ptr() if out.hist is not None else None,
                                     out.n_scored.data_ptr() if out.n_scored is not None else None))
+
+
+def _device_batch_struct(dev_batch, stream=None) -> Batch:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return Batch(dev_batch.n, 1, dev_batch.peak_off.data_ptr(), dev_batch.mz.data_ptr(),
+                 dev_batch.intensity.data_ptr(), dev_batch.prec_mz.data_ptr(), dev_batch.charge.data_ptr(),
+                 dev_batch.tol_da.data_ptr(), s.cuda_stream)
+
+
+class Plan:
+    """Reusable search with scratch allocated once; optionally replayed as a CUDA graph."""
+
+    def __init__(self, index: Index, max_spectra: int, cfg: Optional[SearchConfig] = None):
+        self.index = index
+        h = C.c_void_p()
+        _check(load().hicops_plan_create(index.h, max_spectra, C.byref(cfg) if cfg is not None else None,
+                                         C.byref(h)))
+        self.h = h
+
+    def search(self, dev_batch: "DeviceBatch", out: "DeviceResult", stream=None, graph: bool = True):
+        b = _device_batch_struct(dev_batch, stream)
+        _check(load().hicops_plan_search(self.h, C.byref(b), out.psm.data_ptr(),
+                                         out.hist.data_ptr() if out.hist is not None else None,
+                                         out.n_scored.data_ptr() if out.n_scored is not None else None,
+                                         1 if graph else 0))
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value and _lib is not None:
+            _lib.hicops_plan_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 @dataclass
@@ -289,3 +365,56 @@ class DeviceResult:
         hist = self.hist.cpu().numpy().view(np.uint32).reshape(n, HIST_BINS) if self.hist is not None else None
         ns = self.n_scored.cpu().numpy().view(np.uint32) if self.n_scored is not None else None
         return SearchResult(psm, hist, ns)
+
+
+class Server:
+    """Continuous-batching request server over a resident index."""
+
+    def __init__(self, index: Index, n_slots: int = 0, slot_spectra: int = 0, memory_budget: int = 0):
+        self.index = index
+        self.top_k = index.top_k
+        h = C.c_void_p()
+        cfg = ServerCfg(n_slots, slot_spectra, memory_budget)
+        _check(load().hicops_server_create(index.h, C.byref(cfg), C.byref(h)))
+        self.h = h
+        self._n = {}
+
+    def submit(self, spec) -> int:
+        b, keep = Index._host_batch(spec)
+        t = C.c_uint64()
+        _check(load().hicops_server_submit(self.h, C.byref(b), C.byref(t)))
+        self._n[t.value] = b.n
+        return t.value
+
+    def poll(self, ticket: int, timeout_ms: int = -1) -> Optional[SearchResult]:
+        """Result of a request, or None if it is not done within timeout_ms."""
+        n = self._n[ticket]
+        psm = np.zeros((n, self.top_k), PSM_DTYPE)
+        hist = np.zeros((n, HIST_BINS), np.uint32)
+        ns = np.zeros(n, np.uint32)
+        st = load().hicops_server_poll(self.h, ticket, timeout_ms, _ptr(psm), _ptr(hist), _ptr(ns))
+        if st == ETIMEOUT:
+            return None
+        self._n.pop(ticket, None)
+        _check(st)
+        return SearchResult(psm, hist, ns)
+
+    def cancel(self, ticket: int) -> int:
+        """Status of the cancel: OK, or EBUSY when the request is already launched."""
+        return load().hicops_server_cancel(self.h, ticket)
+
+    def stats(self) -> ServerStats:
+        s = ServerStats()
+        _check(load().hicops_server_get_stats(self.h, C.byref(s)))
+        return s
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value and _lib is not None:
+            _lib.hicops_server_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -88,7 +88,7 @@ def test_parity_tiny_closed_full(gpu, oracle_lib):
     assert n > 900
 
 
-@pytest.mark.parametrize("n_prot,n_spec,tol", [(300, 48, 500.0), (300, 3, 500.0), (200, 40, 100.0)])
+@pytest.mark.parametrize("n_prot,n_spec,tol", [(300, 48, 500.0), (300, 3, 500.0), (1000, 30, 100.0)])
 def test_parity_open_reduced(gpu, oracle_lib, n_prot, n_spec, tol):
     """Open search with modifications on a reduced proteome: windows span
     several 16k-peptide chunks and end in a ragged tail; 3 spectra exercise
