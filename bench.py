@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--oracle-spectra", type=int, default=3, help="CPU-baseline sample size")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--tune-spectra", type=int, default=20000, help="autotuner sample (0 = default shape)")
     return ap.parse_args()
 
 
@@ -232,6 +233,12 @@ def main():
     dev_batch = hc.DeviceBatch.from_spectra(spec)
     out = hc.DeviceResult.alloc(n, k)
     stream = torch.cuda.current_stream()
+    # launch shape from the autotuner, on a sample of the batch
+    t0 = time.perf_counter()
+    tune_batch = hc.DeviceBatch.from_spectra(spec.subset(np.arange(min(n, args.tune_spectra))))
+    shape, tune_ms = idx.autotune(tune_batch) if args.tune_spectra > 0 else (hc.SearchConfig(), 0.0)
+    t_tune = time.perf_counter() - t0
+    del tune_batch
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
     idx.set_timing(True)
     for _ in range(args.warmup):
@@ -329,6 +336,8 @@ def main():
             "phase_ms": {"prep": statistics.mean(prep_ms), "search": statistics.mean(search_ms),
                          "merge": statistics.mean(merge_ms)},
             "step_roofline_spectra_per_s": peak * 1e9 / (step_bytes / n),
+            "launch_shape": shape.as_dict(),
+            "autotune_s": t_tune,
         },
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,

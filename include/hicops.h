@@ -196,14 +196,15 @@ hicops_status hicops_index_copy_csr(const hicops_index* index, uint64_t* off, ui
 /* Launch shape of the search kernel (the paper's R/I/K balancing of
  * superstep 3 becomes the choice of how spectra and peptide ranges map onto
  * persistent CTAs).  Zero fields take the default.  threads: CTA size, 256
- * or 512.  chunk_mult: shared-memory counters per CTA = chunk_mult x 16384
- * peptide ids, 1 or 2.  ctas_per_sm: resident CTAs per SM (0 = as many as
- * fit).  seg_pids: a spectrum's precursor window is split into work units of
- * at least this many peptide ids (0 = split only when the batch is too small
- * to fill the GPU).  Results do not depend on the shape. */
+ * or 512.  chunk_entries: index entries a CTA aims to accumulate per pass
+ * over a range of peptide ids, in units of 1024, 1..6 (default 2); the range
+ * is sized from the spectrum's entry density.  ctas_per_sm: resident CTAs per
+ * SM (0 = as many as fit).  seg_pids: a spectrum's precursor window is split
+ * into work units of at least this many peptide ids (0 = split only when the
+ * batch is too small to fill the GPU).  Results do not depend on the shape. */
 typedef struct hicops_search_config {
     uint32_t threads;
-    uint32_t chunk_mult;
+    uint32_t chunk_entries;
     uint32_t ctas_per_sm;
     uint32_t seg_pids;
 } hicops_search_config;

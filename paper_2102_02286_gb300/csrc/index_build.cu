@@ -440,7 +440,9 @@ hicops_status upload_index(hicops_index* idx) {
     HC_CUDA(cudaMemcpyAsync(&nhot, rtotal, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
     HC_CUDA(cudaStreamSynchronize(s));
     d.n_hot = (uint32_t)nhot;
-    d.hot_words = (P + 31) / 32 + 1;
+    // rows cover every pid of the last search chunk (up to 2 * kChunk past P)
+    // and start 16-byte aligned
+    d.hot_words = ((P + 2ull * kChunk + 31) / 32 + 3) & ~3ull;
     const uint64_t hbytes = sizeof(uint32_t) * (nhot ? nhot : 1) * d.hot_words;
     HC_CUDA(cudaMalloc(&d.hot_b, hbytes));
     HC_CUDA(cudaMalloc(&d.hot_y, hbytes));

@@ -110,7 +110,7 @@ hicops_status sm_count() {
 
 hicops_status check_config(const hicops_search_config& c) {
     if (c.threads != 0 && c.threads != 256 && c.threads != 512) { set_error("threads must be 256 or 512"); return HICOPS_EINVAL; }
-    if (c.chunk_mult > 2) { set_error("chunk_mult must be 1 or 2"); return HICOPS_EINVAL; }
+    if (c.chunk_entries > 6) { set_error("chunk_entries must be in 1..6"); return HICOPS_EINVAL; }
     if (c.ctas_per_sm > 8) { set_error("ctas_per_sm must be <= 8"); return HICOPS_EINVAL; }
     return HICOPS_OK;
 }
@@ -118,7 +118,7 @@ hicops_status check_config(const hicops_search_config& c) {
 hicops_search_config resolved(const hicops_search_config& c) {
     hicops_search_config r = c;
     if (!r.threads) r.threads = 256;
-    if (!r.chunk_mult) r.chunk_mult = 1;
+    if (!r.chunk_entries) r.chunk_entries = 2;
     return r;
 }
 
@@ -133,35 +133,38 @@ uint32_t max_segments(const hicops_search_config& c, uint32_t n) {
 }
 
 template <int KMAX, int THREADS>
-hicops_status launch_search_t(const SearchArgs& sa, uint32_t ctas_per_sm, cudaStream_t s) {
-    static int occ[3] = {-1, -1, -1};
-    const int cm = (int)sa.chunk_mult;
-    const size_t smem = sizeof(uint32_t) * kChunk * cm;
-    if (occ[cm] < 0) {
+hicops_status launch_search_t(const SearchArgs& sa, uint32_t ctas_per_sm, uint64_t max_units, cudaStream_t s) {
+    static int occ = -1;
+    const size_t smem = sizeof(uint32_t) * kChunk;   // 64 KB: the kernel's counters / bit-planes / slots
+    if (occ < 0) {
         HC_CUDA(cudaFuncSetAttribute(search_kernel<KMAX, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(sizeof(uint32_t) * kChunk * 2)));
+                                     (int)smem));
         int b = 0;
         HC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, search_kernel<KMAX, THREADS>, THREADS, smem));
-        occ[cm] = b < 1 ? 1 : b;
+        occ = b < 1 ? 1 : b;
     }
-    int per_sm = occ[cm];
+    int per_sm = occ;
     if (ctas_per_sm && (int)ctas_per_sm < per_sm) per_sm = (int)ctas_per_sm;
-    search_kernel<KMAX, THREADS><<<g_sm_count * per_sm, THREADS, smem, s>>>(sa);
+    // no more CTAs than work units can exist
+    uint64_t grid = (uint64_t)g_sm_count * per_sm;
+    if (max_units < grid) grid = max_units ? max_units : 1;
+    search_kernel<KMAX, THREADS><<<(unsigned)grid, THREADS, smem, s>>>(sa);
     count_launches(1);
     HC_CUDA(cudaGetLastError());
     return HICOPS_OK;
 }
 
-hicops_status launch_search(const SearchArgs& sa, const hicops_search_config& c, cudaStream_t s) {
-    const uint32_t k = sa.k;
-    if (c.threads == 512) {
-        if (k <= 8) return launch_search_t<8, 512>(sa, c.ctas_per_sm, s);
-        if (k <= 16) return launch_search_t<16, 512>(sa, c.ctas_per_sm, s);
-        return launch_search_t<32, 512>(sa, c.ctas_per_sm, s);
-    }
-    if (k <= 8) return launch_search_t<8, 256>(sa, c.ctas_per_sm, s);
-    if (k <= 16) return launch_search_t<16, 256>(sa, c.ctas_per_sm, s);
-    return launch_search_t<32, 256>(sa, c.ctas_per_sm, s);
+template <int THREADS>
+hicops_status launch_search_k(const SearchArgs& sa, uint32_t ctas_per_sm, uint64_t max_units, cudaStream_t s) {
+    if (sa.k <= 8) return launch_search_t<8, THREADS>(sa, ctas_per_sm, max_units, s);
+    if (sa.k <= 16) return launch_search_t<16, THREADS>(sa, ctas_per_sm, max_units, s);
+    return launch_search_t<32, THREADS>(sa, ctas_per_sm, max_units, s);
+}
+
+hicops_status launch_search(const SearchArgs& sa, const hicops_search_config& c, uint64_t max_units,
+                            cudaStream_t s) {
+    if (c.threads == 512) return launch_search_k<512>(sa, c.ctas_per_sm, max_units, s);
+    return launch_search_k<256>(sa, c.ctas_per_sm, max_units, s);
 }
 
 inline void mark(hicops_index* idx, int i, cudaStream_t s, bool on) {
@@ -195,9 +198,10 @@ hicops_status enqueue_search(hicops_index* idx, const DevBatch& d, uint32_t n, c
     HC_CUDA(cudaMemsetAsync(w.work, 0, sizeof(unsigned long long), s));
     SearchArgs sa{w.qbin, w.qiq, w.qn, w.lo, w.hi, w.seg_off, n, p.top_n_peaks, di.off, di.entry,
                   di.skip_row, di.skip, di.skip_stride, di.hot_id, di.hot_b, di.hot_y, di.hot_flags,
-                  di.hot_words, di.lf, di.ls, p.min_shared, k, cfg.chunk_mult, w.utop, d_hist, d_ns, w.work};
+                  di.hot_words, di.lf, di.ls, p.min_shared, k, cfg.chunk_entries * 1024u, w.utop, d_hist, d_ns,
+                  w.work};
     mark(idx, 2, s, timing_marks);
-    hicops_status st = launch_search(sa, cfg, s);
+    hicops_status st = launch_search(sa, cfg, (uint64_t)n * max_seg, s);
     if (st != HICOPS_OK) return st;
     mark(idx, 3, s, timing_marks);
     MergeArgs ma{w.seg_off, w.utop, d_hist, n, k, 0, d_psm};
@@ -443,7 +447,7 @@ extern "C" hicops_status hicops_autotune(hicops_index* idx, const hicops_batch* 
     if (st != HICOPS_OK) return st;
     if (!b->on_device || b->n == 0) { set_error("autotune needs a non-empty device batch"); return HICOPS_EINVAL; }
     const uint32_t cand_threads[2] = {256, 512};
-    const uint32_t cand_cm[2] = {1, 2};
+    const uint32_t cand_cm[2] = {2, 4};   // chunk_entries
     const uint32_t cand_ctas[2] = {0, 1};
     const uint32_t cand_seg[3] = {0, 1u << 18, 1u << 16};
     cudaStream_t s = (cudaStream_t)b->cuda_stream;

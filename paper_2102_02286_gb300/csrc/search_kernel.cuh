@@ -1,28 +1,40 @@
 // filter_2 + score + heap of superstep 3 (paper: Eq. 4 terms k32'..k34,
-// Supplementary Algorithm 3), included by search.cu.
+// Supplementary Algorithm 3), included by search_kernels.cuh.
 //
 // One persistent CTA pulls work units (spectrum q, peptide-id segment) from a
-// device counter.  A segment is walked in chunks of kChunk peptide ids
-// aligned to multiples of kChunk; per chunk:
-//   1. every ordinary peak reads its bucket's run for this chunk from the
-//      chunk skip table (two adjacent words, no search); runs of up to
-//      kShortRun entries are accumulated by the thread that owns the peak,
-//      longer runs are listed and spread over all warps;
-//   2. each entry adds (1 << 26 | iq) for a b ion or (1 << 20 | iq) for a y
-//      ion to the peptide's 32-bit counter in shared memory (nb | ny | S);
-//   3. the epilogue walks the chunk 32 peptides at a time, adds the hot
-//      peaks' contributions from the bucket bitmaps, keeps peptides with
+// device counter.  The segment is cut into super-chunks of whole skip-table
+// columns (kChunk peptide ids each); the number of columns per super-chunk is
+// chosen per unit from the skip tables so that a super-chunk holds about
+// target_entries index entries of the spectrum's ordinary peaks.  Per
+// super-chunk:
+//   1. the run bounds of the next super-chunk are loaded first (their
+//      latency hides behind step 2);
+//   2. every index entry of the super-chunk (all ordinary peaks' runs laid end
+//      to end by a prefix sum) is read once and adds (1 << 26 | iq) for a b ion
+//      or (1 << 20 | iq) for a y ion to the peptide's 32-bit counter
+//      (nb | ny | S), kept in shared memory: directly indexed for a single
+//      column (16384 counters), or in an open-addressing table of 8192
+//      64-bit slots (pid offset << 32 | counter) for wider super-chunks;
+//      slots or counters that become non-zero go to a touched list;
+//   3. the epilogue visits the touched counters, adds the hot peaks'
+//      contributions from the bucket bitmaps, keeps peptides with
 //      nb + ny >= min_shared, ranks them with the exact key
-//      K = LF[nb] + LF[ny] + LS[S], updates the thread's top-k and the
-//      shared histogram, and clears the counters.
-// Hot peaks (buckets holding >= 1/32 of the database, up to kMaxHot per
-// spectrum) never touch the counters: a peptide can only reach min_shared
-// through them alone when the spectrum has >= min_shared hot peaks, which
-// the epilogue checks with the bitmaps.
+//      K = LF[nb] + LF[ny] + LS[S], updates the thread's top-k and the shared
+//      histogram, and clears what it visited.
+// A super-chunk whose entries exceed kMaxEntries is redone column by column
+// with direct counters, so the table never holds more than kMaxEntries keys
+// (< kSlots: probing always ends).  Hot peaks (buckets holding >= 1/32 of
+// the database) never touch the counters; when the spectrum has at least
+// min_shared of them a peptide can qualify through bitmaps alone, and the unit
+// then runs column by column with a dense epilogue that also tests the
+// bitmaps.
 
-constexpr int kMaxHot = 8;
-constexpr int kShortRun = 8;
-constexpr int kMaxWarps = 16;           // CTAs of up to 512 threads
+constexpr int kMaxHot = 6;                 // bitmap slices (b or y bitmap of a hot bucket) per spectrum
+constexpr int kMaxWarps = 16;              // CTAs of up to 512 threads
+constexpr int kTouchCap = 4096;            // touched list of one super-chunk
+constexpr uint32_t kSlots = 8192;          // hash slots: 64 KB, the same bytes as kChunk counters
+constexpr uint32_t kMaxEntries = 6144;     // most entries a hashed super-chunk may hold
+constexpr uint32_t kMaxCols = 64;          // widest super-chunk (columns of kChunk ids)
 
 struct SearchArgs {
     const uint32_t* qbin;
@@ -47,7 +59,7 @@ struct SearchArgs {
     const int64_t* ls;
     uint32_t min_shared;
     uint32_t k;
-    uint32_t chunk_mult;        // counters per CTA = chunk_mult * kChunk
+    uint32_t target_entries;    // entries aimed for per super-chunk
     UnitTop* utop;              // [units * k]
     uint32_t* hist;             // [n * 256]
     uint32_t* nscored;          // [n]
@@ -94,21 +106,26 @@ __device__ __forceinline__ bool better(int64_t ka, uint32_t pa, int64_t kb, uint
 }
 
 struct SearchShared {
-    uint64_t pbase[kMaxTopN];     // bucket start of each ordinary peak
-    uint32_t prow[kMaxTopN];      // its skip-table row
-    uint32_t pinc[kMaxTopN];      // its quantised intensity
-    uint32_t rs[kMaxTopN];        // run start (relative to the bucket) in this chunk
-    uint32_t longp[kMaxTopN];     // peaks with a long run in this chunk
-    uint32_t lpre[kMaxTopN + 1];  // exclusive prefix of the long runs' lengths
-    int32_t hot[kMaxHot];
-    uint32_t hot_inc[kMaxHot];
-    uint32_t hot_fl[kMaxHot];
+    uint64_t pbase[kMaxTopN];         // bucket start of each ordinary peak
+    uint32_t prow[kMaxTopN];          // its skip-table row
+    uint32_t pinc[kMaxTopN];          // its quantised intensity
+    uint32_t pre[2][kMaxTopN + 1];    // exclusive prefix of the run lengths (parity)
+    uint32_t rs[2][kMaxTopN];         // run starts relative to the bucket (parity)
+    union {
+        uint16_t touched[kTouchCap];  // slots / counters that became non-zero
+        uint16_t hotc[kMaxTopN];      // (classification) hot peaks: index into qbin
+    };
+    uint16_t wli[2][kMaxWarps];       // peak holding each warp's first entry (parity)
+    int ntouched;                     // > kTouchCap means the list overflowed
+    const uint32_t* slice[kMaxHot];   // bitmap rows of the spectrum's hot slices
+    uint32_t slice_inc[kMaxHot];      // counter increment of a set bit
     uint32_t hist[kHistBins];
     int64_t lf[kMaxLen + 1];
     int64_t wkey[kMaxWarps];
     uint32_t wpid[kMaxWarps];
     uint32_t wpk[kMaxWarps];
-    int nnorm, nhot, nlong;
+    uint32_t wsum[kMaxWarps];
+    int nnorm, nhotc, nslices, nhotpeaks;
     uint64_t unit;
     uint32_t q, np;
     uint32_t seg_lo, seg_hi;
@@ -118,16 +135,71 @@ __device__ __forceinline__ uint32_t counter_inc(uint32_t e, uint32_t iq) {
     return iq + ((e & 1u) ? (1u << kNyShift) : (1u << kNbShift));
 }
 
-template <int KMAX, int THREADS>
-__global__ void __launch_bounds__(THREADS) search_kernel(SearchArgs a) {
-    extern __shared__ __align__(16) uint32_t cnt[];   // chunk_mult * kChunk counters
-    __shared__ SearchShared sh;
+__device__ __forceinline__ uint32_t slot_of(uint32_t off) { return (off * 2654435761u) >> 19; }   // 13 bits
+
+// Exclusive scan of the ordinary peaks' run lengths, in two halves around a
+// barrier the caller provides.  Thread tid owns peaks tid*ppt .. +ppt-1.
+template <int PPT>
+__device__ __forceinline__ uint32_t scan_runs_1(SearchShared& sh, int nnorm, int ppt, const uint32_t (&ra)[PPT],
+                                                const uint32_t (&rb)[PPT]) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t sum = 0;
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+        const int t = tid * ppt + i;
+        if (i < ppt && t < nnorm) sum += rb[i] - ra[i];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t x = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += x;
+    }
+    if (lane == 31) sh.wsum[warp] = incl;
+    return incl - sum;
+}
+
+template <int THREADS, int PPT>
+__device__ __forceinline__ void scan_runs_2(SearchShared& sh, int buf, int nnorm, int ppt, uint32_t excl,
+                                            const uint32_t (&ra)[PPT], const uint32_t (&rb)[PPT]) {
+    const int tid = threadIdx.x, warp = tid >> 5;
     constexpr int nwarps = THREADS / 32;
-    const uint32_t cm = a.chunk_mult;
-    const uint32_t span = kChunk * cm;
+    uint32_t wbase = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < nwarps; ++w) {
+        const uint32_t s = sh.wsum[w];
+        if (w < warp) wbase += s;
+        total += s;
+    }
+    const uint32_t per = (total + nwarps - 1) / nwarps;
+    uint32_t run = wbase + excl;
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+        const int t = tid * ppt + i;
+        if (i < ppt && t < nnorm) {
+            const uint32_t len = rb[i] - ra[i];
+            sh.pre[buf][t] = run;
+            sh.rs[buf][t] = ra[i];
+            if (len)   // warps whose share starts inside this run
+                for (uint32_t w = (run + per - 1) / per; w * per < run + len && w < (uint32_t)nwarps; ++w)
+                    sh.wli[buf][w] = (uint16_t)t;
+            run += len;
+        }
+    }
+    if (tid == 0) sh.pre[buf][nnorm] = total;
+}
+
+template <int KMAX, int THREADS>
+__global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel(SearchArgs a) {
+    extern __shared__ __align__(16) unsigned long long tab[];   // kSlots slots, or 2 * kSlots direct counters
+    uint32_t* const cnt = reinterpret_cast<uint32_t*>(tab);
+    __shared__ SearchShared sh;
+    constexpr int nwarps = THREADS / 32;
+    constexpr int PPT = kMaxTopN / THREADS;             // ordinary peaks per thread (at most)
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
     const uint32_t last_col = a.skip_stride - 1;
-    for (int i = tid; i < (int)span; i += THREADS) cnt[i] = 0;
+    for (int i = tid; i < (int)kSlots; i += THREADS) tab[i] = 0ull;
     for (int i = tid; i < (int)kHistBins; i += THREADS) sh.hist[i] = 0;
     for (int i = tid; i <= (int)kMaxLen; i += THREADS) sh.lf[i] = a.lf[i];
     const uint64_t total_units = a.seg_off[a.n];
@@ -139,7 +211,10 @@ __global__ void __launch_bounds__(THREADS) search_kernel(SearchArgs a) {
             const uint64_t u = atomicAdd(a.work, 1ull);
             sh.unit = u;
             sh.nnorm = 0;
-            sh.nhot = 0;
+            sh.nhotc = 0;
+            sh.nslices = 0;
+            sh.nhotpeaks = 0;
+            sh.ntouched = 0;
             if (u < total_units) {
                 // spectrum owning unit u: last q with seg_off[q] <= u
                 uint32_t lo_q = 0, hi_q = a.n;
@@ -162,164 +237,289 @@ __global__ void __launch_bounds__(THREADS) search_kernel(SearchArgs a) {
         const uint64_t u = sh.unit;
         if (u >= total_units) break;
         const uint32_t q = sh.q, np = sh.np, seg_lo = sh.seg_lo, seg_hi = sh.seg_hi;
-        // classify the retained peaks: hot (bitmap) or ordinary (skip table)
+        // classify the retained peaks: hot (bitmap) candidates or ordinary (skip table)
         for (uint32_t t = tid; t < np; t += THREADS) {
             const uint32_t bin = a.qbin[(uint64_t)q * a.topn + t];
-            const uint32_t iq = a.qiq[(uint64_t)q * a.topn + t];
-            const int32_t hid = a.hot_id[bin];
-            if (hid >= 0) {
-                const int s = atomicAdd(&sh.nhot, 1);
-                if (s < kMaxHot) {
-                    sh.hot[s] = hid;
-                    sh.hot_inc[s] = iq;
-                    sh.hot_fl[s] = a.hot_flags[hid];
-                    continue;
-                }
+            if (a.hot_id[bin] >= 0) {
+                sh.hotc[atomicAdd(&sh.nhotc, 1)] = (uint16_t)t;
+                continue;
             }
             const int32_t row = a.skip_row[bin];
             if (row < 0) continue;   // empty bucket
             const int s = atomicAdd(&sh.nnorm, 1);
             sh.pbase[s] = a.off[bin];
             sh.prow[s] = (uint32_t)row;
-            sh.pinc[s] = iq;
+            sh.pinc[s] = a.qiq[(uint64_t)q * a.topn + t];
+        }
+        __syncthreads();
+        if (tid == 0) {
+            // bitmap slices in peak order while they last; the rest are ordinary
+            int ns = 0, nh = 0;
+            for (int c = 0; c < sh.nhotc; ++c) {
+                const uint32_t t = sh.hotc[c];
+                const uint32_t bin = a.qbin[(uint64_t)q * a.topn + t];
+                const uint32_t iq = a.qiq[(uint64_t)q * a.topn + t];
+                const int32_t hid = a.hot_id[bin];
+                const uint32_t fl = a.hot_flags[hid];
+                const int need = (fl & 1u ? 1 : 0) + (fl & 2u ? 1 : 0);
+                if (ns + need <= kMaxHot) {
+                    if (fl & 1u) { sh.slice[ns] = a.hot_b + (uint64_t)hid * a.hot_words; sh.slice_inc[ns++] = (1u << kNbShift) + iq; }
+                    if (fl & 2u) { sh.slice[ns] = a.hot_y + (uint64_t)hid * a.hot_words; sh.slice_inc[ns++] = (1u << kNyShift) + iq; }
+                    ++nh;
+                } else {
+                    const int s = sh.nnorm++;
+                    sh.pbase[s] = a.off[bin];
+                    sh.prow[s] = (uint32_t)a.skip_row[bin];
+                    sh.pinc[s] = iq;
+                }
+            }
+            sh.nslices = ns;
+            sh.nhotpeaks = nh;
+        }
+        __syncthreads();
+        const int nnorm = sh.nnorm, nslices = sh.nslices;
+        const bool hot_alone = sh.nhotpeaks >= (int)min_shared;
+        const int ppt = (nnorm + THREADS - 1) / THREADS;
+        const uint32_t col_lo = seg_lo >> kChunkShift, col_end = ((seg_hi - 1) >> kChunkShift) + 1;
+        uint32_t ra[PPT], rb[PPT];
+        auto load_runs = [&](uint32_t c0l, uint32_t c1l) {
+#pragma unroll
+            for (int i = 0; i < PPT; ++i) {
+                const int t = tid * ppt + i;
+                ra[i] = rb[i] = 0;
+                if (i < ppt && t < nnorm) {
+                    const uint32_t* sk = a.skip + (uint64_t)sh.prow[t] * a.skip_stride;
+                    ra[i] = __ldg(sk + c0l);
+                    rb[i] = __ldg(sk + min(c1l, last_col));
+                }
+            }
+        };
+        // columns per super-chunk, from the segment's total entries
+        uint32_t m = 1;
+        {
+            load_runs(col_lo, col_end);
+            uint32_t s = 0;
+#pragma unroll
+            for (int i = 0; i < PPT; ++i) s += rb[i] - ra[i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) sh.wsum[warp] = s;
+            __syncthreads();
+            uint32_t total = 0;
+#pragma unroll
+            for (int w = 0; w < nwarps; ++w) total += sh.wsum[w];
+            const uint32_t ncols = col_end - col_lo;
+            if (!hot_alone) {
+                uint64_t want = total ? ((uint64_t)a.target_entries * ncols) / total : ncols;
+                if (want < 1) want = 1;
+                if (want > kMaxCols) want = kMaxCols;
+                m = min((uint32_t)want, ncols);
+            }
+            __syncthreads();   // wsum is reused by the scans
         }
         TopK<KMAX> top;
         top.init();
-        __syncthreads();
-        const int nhot = min(sh.nhot, kMaxHot);
-        const int nnorm = sh.nnorm;
-        const uint32_t j_first = (seg_lo >> kChunkShift) / cm, j_last = ((seg_hi - 1) >> kChunkShift) / cm;
-        for (uint32_t j = j_first; j <= j_last; ++j) {
-            const uint32_t cbase = (j * cm) << kChunkShift;
-            const uint32_t c0 = max(seg_lo, cbase), c1 = min(seg_hi, cbase + span);
-            const uint32_t col0 = j * cm, col1 = min(col0 + cm, last_col);
-            if (tid == 0) sh.nlong = 0;
-            __syncthreads();
-            // 1. runs of this chunk; short runs accumulated here
-            for (int t = tid; t < nnorm; t += THREADS) {
-                const uint32_t* sk = a.skip + (uint64_t)sh.prow[t] * a.skip_stride;
-                const uint32_t ra = __ldg(sk + col0), rb = __ldg(sk + col1);
-                const uint32_t len = rb - ra;
-                if (len <= (uint32_t)kShortRun) {
-                    const uint32_t* ep = a.entry + sh.pbase[t] + ra;
-                    uint32_t v[kShortRun];
-#pragma unroll
-                    for (int i = 0; i < kShortRun; ++i) v[i] = (uint32_t)i < len ? __ldg(ep + i) : 0xffffffffu;
-                    const uint32_t iq = sh.pinc[t];
-#pragma unroll
-                    for (int i = 0; i < kShortRun; ++i) {
-                        const uint32_t pid = v[i] >> 1;
-                        if ((uint32_t)i < len && pid >= c0 && pid < c1) atomicAdd(&cnt[pid - cbase], counter_inc(v[i], iq));
-                    }
-                } else {
-                    const int s = atomicAdd(&sh.nlong, 1);
-                    sh.longp[s] = (uint32_t)t;
-                    sh.rs[t] = ra;
-                    sh.lpre[s + 1] = len;
-                }
+
+        // entries of super-chunk [cbase, cbase + span) clipped to [x0, x1);
+        // direct counters when dense, otherwise the hash table
+        auto accumulate = [&](int buf, uint32_t cbase, uint32_t x0, uint32_t x1, bool dense) {
+            const uint32_t R = sh.pre[buf][nnorm];
+            const uint32_t per = (R + nwarps - 1) / nwarps;
+            const uint32_t f0 = (uint32_t)warp * per, f1 = min(R, f0 + per);
+            int li = 0;
+            if (f0 < f1) {
+                li = sh.wli[buf][warp];
+                const uint32_t fs = f0 + lane;
+                if (fs < f1)
+                    while (sh.pre[buf][li + 1] <= fs) ++li;
             }
-            __syncthreads();
-            // 2. long runs spread over the warps
-            const int nl = sh.nlong;
-            if (nl > 0) {
-                if (warp == 0) {
-                    uint32_t carry = 0;
-                    for (int b = 0; b < nl; b += 32) {
-                        const int i = b + lane;
-                        uint32_t v = i < nl ? sh.lpre[i + 1] : 0u;
+            for (uint32_t fb = f0; fb < f1; fb += 4 * 32) {   // uniform across the warp
+                uint32_t e[4], inc[4];
 #pragma unroll
-                        for (int o = 1; o < 32; o <<= 1) {
-                            const uint32_t x = __shfl_up_sync(0xffffffffu, v, o);
-                            if (lane >= o) v += x;
+                for (int r = 0; r < 4; ++r) {
+                    const uint32_t ff = fb + r * 32 + lane;
+                    e[r] = 0xffffffffu;
+                    inc[r] = 0;
+                    if (ff < f1) {
+                        while (sh.pre[buf][li + 1] <= ff) ++li;
+                        e[r] = __ldg(a.entry + sh.pbase[li] + sh.rs[buf][li] + (ff - sh.pre[buf][li]));
+                        inc[r] = sh.pinc[li];
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const uint32_t pid = e[r] >> 1;
+                    const bool act = pid >= x0 && pid < x1;
+                    bool first = false;
+                    uint32_t where = 0;
+                    if (act) {
+                        const uint32_t off = pid - cbase;
+                        const uint32_t v = counter_inc(e[r], inc[r]);
+                        if (dense) {
+                            first = atomicAdd(&cnt[off], v) == 0u;
+                            where = off;
+                        } else {
+                            const unsigned long long item = ((unsigned long long)off << 32) | v;
+                            uint32_t sl = slot_of(off);
+                            for (uint32_t probe = 0; probe < kSlots; ++probe) {
+                                const unsigned long long old = atomicCAS(&tab[sl], 0ull, item);
+                                if (old == 0ull) { first = true; break; }
+                                if ((uint32_t)(old >> 32) == off) { atomicAdd(&tab[sl], (unsigned long long)v); break; }
+                                sl = (sl + 1) & (kSlots - 1);
+                            }
+                            where = sl;
                         }
-                        if (i < nl) sh.lpre[i + 1] = carry + v;
-                        carry += __shfl_sync(0xffffffffu, v, 31);
                     }
-                    if (lane == 0) sh.lpre[0] = 0;
-                }
-                __syncthreads();
-                const uint32_t R = sh.lpre[nl];
-                const uint32_t per = (R + nwarps - 1) / nwarps;
-                const uint32_t f0 = (uint32_t)warp * per, f1 = min(R, f0 + per);
-                if (f0 + lane < f1) {
-                    // long run holding flat index f0 + lane
-                    int li = 0, hi_i = nl;
-                    const uint32_t fs = f0 + lane;
-                    while (hi_i - li > 1) {
-                        const int m = (li + hi_i) >> 1;
-                        if (sh.lpre[m] <= fs) li = m; else hi_i = m;
-                    }
-                    for (uint32_t f = fs; f < f1; f += 32) {
-                        while (sh.lpre[li + 1] <= f) ++li;
-                        const uint32_t t = sh.longp[li];
-                        const uint32_t e = __ldg(a.entry + sh.pbase[t] + sh.rs[t] + (f - sh.lpre[li]));
-                        const uint32_t pid = e >> 1;
-                        if (pid >= c0 && pid < c1) atomicAdd(&cnt[pid - cbase], counter_inc(e, sh.pinc[t]));
+                    const unsigned bal = __ballot_sync(0xffffffffu, first);
+                    if (bal) {
+                        const int leader = __ffs(bal) - 1;
+                        int base = 0;
+                        if (lane == leader) base = atomicAdd(&sh.ntouched, __popc(bal));
+                        base = __shfl_sync(0xffffffffu, base, leader);
+                        const int slot = base + __popc(bal & lt);
+                        if (first && slot < kTouchCap) sh.touched[slot] = (uint16_t)where;
                     }
                 }
             }
-            __syncthreads();
-            // 3. epilogue, 32 peptide ids per step
-            const uint32_t g0 = (c0 - cbase) >> 5, g1 = (c1 - cbase + 31) >> 5;
-            for (uint32_t g = g0 + tid; g < g1; g += THREADS) {
-                const uint32_t gp = cbase + (g << 5);
-                uint4* c4 = reinterpret_cast<uint4*>(&cnt[g << 5]);
-                uint32_t nz = 0;
-                uint32_t nzq = 0;   // which of the 8 uint4 words are non-zero
-#pragma unroll
-                for (int w4 = 0; w4 < 8; ++w4) {
-                    const uint4 v = c4[w4];
-                    const uint32_t m = (v.x ? 1u : 0u) | (v.y ? 2u : 0u) | (v.z ? 4u : 0u) | (v.w ? 8u : 0u);
-                    nz |= m << (4 * w4);
-                    nzq |= (m ? 1u : 0u) << w4;
-                }
-                const uint32_t lo_b = c0 > gp ? c0 - gp : 0u;
-                const uint32_t hi_b = c1 - gp >= 32u ? 32u : c1 - gp;
-                const uint32_t valid = (hi_b >= 32u ? 0xffffffffu : ((1u << hi_b) - 1u)) & ~((1u << lo_b) - 1u);
-                uint32_t wb[kMaxHot], wy[kMaxHot];
-                const uint64_t word = gp >> 5;
-#pragma unroll
-                for (int h = 0; h < kMaxHot; ++h) {
-                    wb[h] = 0;
-                    wy[h] = 0;
-                    if (h < nhot) {
-                        const uint64_t o = (uint64_t)sh.hot[h] * a.hot_words + word;
-                        if (sh.hot_fl[h] & 1u) wb[h] = __ldg(a.hot_b + o) & valid;
-                        if (sh.hot_fl[h] & 2u) wy[h] = __ldg(a.hot_y + o) & valid;
+        };
+        auto score = [&](uint32_t c, uint32_t pid) {
+            const uint32_t nb = c >> kNbShift, ny = (c >> kNyShift) & 63u;
+            if (nb + ny >= min_shared) {
+                const uint32_t S = c & kSMask;
+                const int64_t K = sh.lf[nb] + sh.lf[ny] + __ldg(a.ls + S);
+                const int64_t hb = K >> 31;
+                atomicAdd(&sh.hist[hb > 255 ? 255 : (hb < 0 ? 0 : hb)], 1u);
+                top.insert(K, pid, c, k);
+            }
+        };
+        // one counter (c, pid): filter, add the hot slices, score
+        auto visit = [&](uint32_t c, uint32_t pid) {
+            const uint32_t nn = (c >> kNbShift) + ((c >> kNyShift) & 63u);
+            if (nn + (uint32_t)nslices < min_shared) return;
+            for (int s = 0; s < nslices; ++s)
+                if ((__ldg(sh.slice[s] + (pid >> 5)) >> (pid & 31)) & 1u) c += sh.slice_inc[s];
+            score(c, pid);
+        };
+        // epilogue of a super-chunk; clears what it visits
+        auto epilogue = [&](uint32_t cbase, uint32_t x0, uint32_t x1, bool dense) {
+            const int nt = sh.ntouched;
+            if (nt <= kTouchCap && !hot_alone) {
+                for (int i = tid; i < nt; i += THREADS) {
+                    const uint32_t w = sh.touched[i];
+                    if (dense) {
+                        const uint32_t c = cnt[w];
+                        cnt[w] = 0u;
+                        visit(c, cbase + w);
+                    } else {
+                        const unsigned long long v = tab[w];
+                        tab[w] = 0ull;
+                        visit((uint32_t)v, cbase + (uint32_t)(v >> 32));
                     }
                 }
-                uint32_t cand = nz & valid;
-                if (nhot >= (int)min_shared) {
-                    // peptides reaching min_shared through hot peaks alone
-                    for (int jb = 0; jb < 32; ++jb) {
+            } else if (!dense) {
+                for (uint32_t i = tid; i < kSlots; i += THREADS) {
+                    const unsigned long long v = tab[i];
+                    if (v == 0ull) continue;
+                    tab[i] = 0ull;
+                    visit((uint32_t)v, cbase + (uint32_t)(v >> 32));
+                }
+            } else {
+                // every counter of the column, 32 peptide ids per step; with
+                // >= min_shared hot peaks the bitmaps alone can qualify a peptide
+                for (uint32_t gi = tid; gi < kChunk / 32; gi += THREADS) {
+                    const uint32_t gp = cbase + (gi << 5);
+                    if (gp + 32 <= x0 || gp >= x1) continue;
+                    const uint32_t lo_b = x0 > gp ? x0 - gp : 0u;
+                    const uint32_t hi_b = x1 - gp >= 32u ? 32u : x1 - gp;
+                    const uint32_t valid = (hi_b >= 32u ? 0xffffffffu : ((1u << hi_b) - 1u)) & ~((1u << lo_b) - 1u);
+                    uint32_t hw[kMaxHot];
+#pragma unroll
+                    for (int s = 0; s < kMaxHot; ++s) hw[s] = s < nslices ? __ldg(sh.slice[s] + (gp >> 5)) : 0u;
+                    uint32_t cand = 0;
+                    for (int j = 0; j < 32; ++j) {
+                        const int jb = (j + lane) & 31;   // rotated: lanes hit different banks
+                        const uint32_t c = cnt[(gi << 5) + jb];
                         uint32_t hc = 0;
 #pragma unroll
-                        for (int h = 0; h < kMaxHot; ++h) hc += ((wb[h] | wy[h]) >> jb) & 1u;
-                        if (hc >= min_shared) cand |= 1u << jb;
+                        for (int s = 0; s < kMaxHot; ++s) hc += (hw[s] >> jb) & 1u;
+                        const uint32_t nn = (c >> kNbShift) + ((c >> kNyShift) & 63u);
+                        if ((c != 0u || hc > 0u) && nn + hc >= min_shared) cand |= 1u << jb;
                     }
-                }
-                while (cand) {
-                    const int jb = __ffs(cand) - 1;
-                    cand &= cand - 1;
-                    uint32_t c = cnt[(g << 5) + jb];
+                    cand &= valid;
+                    while (cand) {
+                        const int jb = __ffs(cand) - 1;
+                        cand &= cand - 1;
+                        uint32_t c = cnt[(gi << 5) + jb];
 #pragma unroll
-                    for (int h = 0; h < kMaxHot; ++h) {
-                        if ((wb[h] >> jb) & 1u) c += (1u << kNbShift) + sh.hot_inc[h];
-                        if ((wy[h] >> jb) & 1u) c += (1u << kNyShift) + sh.hot_inc[h];
+                        for (int s = 0; s < kMaxHot; ++s)
+                            if ((hw[s] >> jb) & 1u) c += sh.slice_inc[s];
+                        score(c, gp + jb);
                     }
-                    const uint32_t nb = c >> kNbShift, ny = (c >> kNyShift) & 63u;
-                    if (nb + ny >= min_shared) {
-                        const uint32_t S = c & kSMask;
-                        const int64_t K = sh.lf[nb] + sh.lf[ny] + __ldg(a.ls + S);
-                        const int64_t hb = K >> 31;
-                        atomicAdd(&sh.hist[hb > 255 ? 255 : (hb < 0 ? 0 : hb)], 1u);
-                        top.insert(K, gp + jb, c, k);
-                    }
+#pragma unroll 4
+                    for (int j = 0; j < 32; ++j) cnt[(gi << 5) + ((j + lane) & 31)] = 0u;
                 }
-#pragma unroll
-                for (int w4 = 0; w4 < 8; ++w4)
-                    if ((nzq >> w4) & 1u) c4[w4] = make_uint4(0, 0, 0, 0);
             }
+        };
+
+        // prologue: bounds of the first super-chunk
+        uint32_t c = col_lo;
+        uint32_t e = min(col_lo + m, col_end);
+        int buf = 0;
+        load_runs(c, e);
+        {
+            const uint32_t excl = scan_runs_1<PPT>(sh, nnorm, ppt, ra, rb);
+            __syncthreads();
+            scan_runs_2<THREADS, PPT>(sh, buf, nnorm, ppt, excl, ra, rb);
+        }
+        __syncthreads();
+        while (c < col_end) {
+            const uint32_t R = sh.pre[buf][nnorm];
+            if (R > kMaxEntries && e - c > 1) {
+                // too many entries for the table: this super-chunk column by column
+                for (uint32_t cc = c; cc < e; ++cc) {
+                    load_runs(cc, cc + 1);
+                    const uint32_t excl = scan_runs_1<PPT>(sh, nnorm, ppt, ra, rb);
+                    __syncthreads();
+                    scan_runs_2<THREADS, PPT>(sh, buf ^ 1, nnorm, ppt, excl, ra, rb);
+                    __syncthreads();
+                    const uint32_t cb = cc << kChunkShift;
+                    const uint32_t x0 = max(seg_lo, cb), x1 = min(seg_hi, cb + kChunk);
+                    accumulate(buf ^ 1, cb, x0, x1, true);
+                    __syncthreads();
+                    epilogue(cb, x0, x1, true);
+                    __syncthreads();
+                    if (tid == 0) sh.ntouched = 0;
+                    __syncthreads();
+                }
+                c = e;
+                if (c < col_end) {
+                    e = min(c + m, col_end);
+                    load_runs(c, e);
+                    const uint32_t excl = scan_runs_1<PPT>(sh, nnorm, ppt, ra, rb);
+                    __syncthreads();
+                    scan_runs_2<THREADS, PPT>(sh, buf, nnorm, ppt, excl, ra, rb);
+                    __syncthreads();
+                }
+                continue;
+            }
+            const bool dense = (e - c) == 1;
+            const uint32_t cbase = c << kChunkShift;
+            const uint32_t x0 = max(seg_lo, cbase), x1 = min(seg_hi, e << kChunkShift);
+            const uint32_t nc = e, ne = min(e + m, col_end);
+            const bool more = nc < col_end;
+            if (more) load_runs(nc, ne);                 // next super-chunk's bounds
+            accumulate(buf, cbase, x0, x1, dense);
+            uint32_t excl = 0;
+            if (more) excl = scan_runs_1<PPT>(sh, nnorm, ppt, ra, rb);
+            __syncthreads();
+            epilogue(cbase, x0, x1, dense);
+            if (more) scan_runs_2<THREADS, PPT>(sh, buf ^ 1, nnorm, ppt, excl, ra, rb);
+            __syncthreads();
+            if (tid == 0) sh.ntouched = 0;
+            buf ^= 1;
+            c = nc;
+            e = ne;
+            // the next accumulate appends to ntouched: make the reset visible
             __syncthreads();
         }
         // block top-k: k rounds of block-wide argmax over the thread heads

@@ -58,7 +58,7 @@ class IndexStats(C.Structure):
 
 
 class SearchConfig(C.Structure):
-    _fields_ = [("threads", C.c_uint32), ("chunk_mult", C.c_uint32), ("ctas_per_sm", C.c_uint32),
+    _fields_ = [("threads", C.c_uint32), ("chunk_entries", C.c_uint32), ("ctas_per_sm", C.c_uint32),
                 ("seg_pids", C.c_uint32)]
 
     def as_dict(self):

@@ -34,11 +34,11 @@ def same(a, b):
 
 
 @pytest.mark.parametrize("threads", [256, 512])
-@pytest.mark.parametrize("chunk_mult", [1, 2])
+@pytest.mark.parametrize("chunk_entries", [1, 2, 6])
 @pytest.mark.parametrize("seg_pids", [0, 1 << 14, 1 << 16])
-def test_launch_shapes_identical(setup, threads, chunk_mult, seg_pids):
+def test_launch_shapes_identical(setup, threads, chunk_entries, seg_pids):
     torch, w, prot, idx, spec, ref = setup
-    idx.set_config(hc.SearchConfig(threads, chunk_mult, 0, seg_pids))
+    idx.set_config(hc.SearchConfig(threads, chunk_entries, 0, seg_pids))
     try:
         same(idx.search(spec), ref)
     finally:
@@ -74,7 +74,9 @@ def test_plan_small_batch_splits_windows(setup, oracle_lib):
     plan.search(db, out, torch.cuda.current_stream(), graph=False)
     torch.cuda.synchronize()
     got = out.to_host(sub.n, w.params.top_k)
-    np.testing.assert_array_equal(got.psm, ref.psm[[3, 7]])
+    exp = ref.psm[[3, 7]].copy()
+    exp["query"] = np.arange(2)[:, None]        # rows carry the index within their own batch
+    np.testing.assert_array_equal(got.psm, exp)
     np.testing.assert_array_equal(got.hist, ref.hist[[3, 7]])
     odb = oracle_lib.OracleDb(prot.seq, prot.off, w.mods, w.params)
     assert_parity(got, odb.search(sub), label="plan small batch")
@@ -85,7 +87,7 @@ def test_autotune_keeps_results(setup):
     torch, w, prot, idx, spec, ref = setup
     db = hc.DeviceBatch.from_spectra(spec)
     best, ms = idx.autotune(db)
-    assert best.threads in (256, 512) and best.chunk_mult in (1, 2) and ms > 0
+    assert best.threads in (256, 512) and 1 <= best.chunk_entries <= 6 and ms > 0
     try:
         same(idx.search(spec), ref)
     finally:
