@@ -198,7 +198,7 @@ hicops_status enqueue_search(hicops_index* idx, const DevBatch& d, uint32_t n, c
     HC_CUDA(cudaMemsetAsync(w.work, 0, sizeof(unsigned long long), s));
     SearchArgs sa{w.qbin, w.qiq, w.qn, w.lo, w.hi, w.seg_off, n, p.top_n_peaks, di.off, di.entry,
                   di.skip_row, di.skip, di.skip_stride, di.hot_id, di.hot_b, di.hot_y, di.hot_flags,
-                  di.hot_words, di.lf, di.ls, p.min_shared, k, cfg.chunk_entries * 1024u, w.utop, d_hist, d_ns,
+                  di.hot_words, di.lf, di.ls, (uint32_t)idx->s_max, p.min_shared, k, cfg.chunk_entries * 1024u, w.utop, d_hist, d_ns,
                   w.work};
     mark(idx, 2, s, timing_marks);
     hicops_status st = launch_search(sa, cfg, (uint64_t)n * max_seg, s);

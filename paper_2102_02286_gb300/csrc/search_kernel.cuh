@@ -3,38 +3,53 @@
 //
 // One persistent CTA pulls work units (spectrum q, peptide-id segment) from a
 // device counter.  The segment is cut into super-chunks of whole skip-table
-// columns (kChunk peptide ids each); the number of columns per super-chunk is
-// chosen per unit from the skip tables so that a super-chunk holds about
-// target_entries index entries of the spectrum's ordinary peaks.  Per
-// super-chunk:
-//   1. the run bounds of the next super-chunk are loaded first (their
-//      latency hides behind step 2);
-//   2. every index entry of the super-chunk (all ordinary peaks' runs laid end
-//      to end by a prefix sum) is read once and adds (1 << 26 | iq) for a b ion
-//      or (1 << 20 | iq) for a y ion to the peptide's 32-bit counter
-//      (nb | ny | S), kept in shared memory: directly indexed for a single
-//      column (16384 counters), or in an open-addressing table of 8192
-//      64-bit slots (pid offset << 32 | counter) for wider super-chunks;
-//      slots or counters that become non-zero go to a touched list;
-//   3. the epilogue visits the touched counters, adds the hot peaks'
-//      contributions from the bucket bitmaps, keeps peptides with
-//      nb + ny >= min_shared, ranks them with the exact key
-//      K = LF[nb] + LF[ny] + LS[S], updates the thread's top-k and the shared
-//      histogram, and clears what it visited.
-// A super-chunk whose entries exceed kMaxEntries is redone column by column
-// with direct counters, so the table never holds more than kMaxEntries keys
-// (< kSlots: probing always ends).  Hot peaks (buckets holding >= 1/32 of
-// the database) never touch the counters; when the spectrum has at least
-// min_shared of them a peptide can qualify through bitmaps alone, and the unit
-// then runs column by column with a dense epilogue that also tests the
-// bitmaps.
+// columns (kChunk peptide ids each, at most kMaxCols); the columns per
+// super-chunk are chosen per unit from the skip tables so that a super-chunk
+// holds about target_entries index entries of the spectrum's ordinary peaks.
+//
+// Almost every peptide in a precursor window is hit by at most one ordinary
+// peak, and with fewer than min_shared - 1 hot slices such a peptide cannot
+// reach min_shared.  So a super-chunk is searched as:
+//   pass A  every index entry (all ordinary peaks' runs laid end to end by a
+//           prefix sum; lane l of a warp takes entries l, l + 32, ...) sets
+//           the peptide's bit in a "seen" bit-plane and, when it was set, in
+//           a "twice" plane (shared-memory atomicOr), and is logged in shared
+//           memory as (peptide offset | isY << 17 | peak << 18); first bits
+//           set in the twice plane are counted;
+//   mark    only when nslices >= min_shared - 1 (peptides seen once with
+//           enough hot bits are candidates too) or when there are more than
+//           kRound candidates: the planes are scanned, candidates counted and
+//           split into rounds of at most kRound candidates by runs of whole
+//           plane words; otherwise there is one round of the twice plane;
+//   replay  per round, the log is walked and every entry of a candidate adds
+//           (1 << 26 | iq) for a b ion or (1 << 20 | iq) for a y ion to the
+//           peptide's 32-bit counter (nb | ny | S) in an open-addressing
+//           table of kSlots 64-bit slots (offset << 32 | counter); a round has
+//           fewer than kSlots keys, so probing always ends;
+//   epilogue the occupied slots get the hot peaks' contributions from the
+//           bucket bitmaps; peptides with nb + ny >= min_shared are ranked
+//           with the exact key K = LF[nb] + LF[ny] + LS[S] into the thread's
+//           top-k and the shared histogram.
+// A super-chunk with more than kMaxEntries entries is searched column by
+// column with 16384 directly indexed counters, and so is every column of a
+// unit whose spectrum has >= min_shared hot peaks (bitmaps alone can qualify
+// a peptide; that epilogue scans every counter and the bitmaps).
 
 constexpr int kMaxHot = 6;                 // bitmap slices (b or y bitmap of a hot bucket) per spectrum
 constexpr int kMaxWarps = 16;              // CTAs of up to 512 threads
-constexpr int kTouchCap = 4096;            // touched list of one super-chunk
-constexpr uint32_t kSlots = 8192;          // hash slots: 64 KB, the same bytes as kChunk counters
-constexpr uint32_t kMaxEntries = 6144;     // most entries a hashed super-chunk may hold
-constexpr uint32_t kMaxCols = 64;          // widest super-chunk (columns of kChunk ids)
+constexpr int kTouchCap = 4096;            // touched list of a direct-counter column
+constexpr uint32_t kMaxCols = 8;           // widest super-chunk (columns of kChunk ids)
+constexpr uint32_t kPlaneWords = kMaxCols * kChunk / 32;   // 4096 words per bit-plane
+constexpr uint32_t kMaxEntries = 6144;     // log capacity (entries of one super-chunk)
+constexpr uint32_t kSlots = 1024;          // candidate counters per round
+constexpr uint32_t kRound = 768;           // candidates per round (+31 at most)
+constexpr uint32_t kMaxRounds = kMaxEntries / kRound + 2;
+// 64 KB of dynamic shared memory, in 32-bit words:
+//   [0, 4096) seen plane | [4096, 8192) twice plane | [8192, 14336) log |
+//   [14336, 16384) kSlots 64-bit slots;  or 16384 direct counters
+constexpr uint32_t kLogWord = 2 * kPlaneWords;
+constexpr uint32_t kSlotWord = kLogWord + kMaxEntries;
+static_assert(kSlotWord + 2 * kSlots == kChunk, "shared-memory layout must fill 64 KB");
 
 struct SearchArgs {
     const uint32_t* qbin;
@@ -57,6 +72,7 @@ struct SearchArgs {
     uint64_t hot_words;
     const int64_t* lf;
     const int64_t* ls;
+    uint32_t s_max;             // last valid index of ls
     uint32_t min_shared;
     uint32_t k;
     uint32_t target_entries;    // entries aimed for per super-chunk
@@ -112,11 +128,14 @@ struct SearchShared {
     uint32_t pre[2][kMaxTopN + 1];    // exclusive prefix of the run lengths (parity)
     uint32_t rs[2][kMaxTopN];         // run starts relative to the bucket (parity)
     union {
-        uint16_t touched[kTouchCap];  // slots / counters that became non-zero
+        uint16_t touched[kTouchCap];  // counters that became non-zero (direct columns)
         uint16_t hotc[kMaxTopN];      // (classification) hot peaks: index into qbin
     };
     uint16_t wli[2][kMaxWarps];       // peak holding each warp's first entry (parity)
+    uint16_t wb[kMaxRounds + 1];      // first plane word of each candidate round
     int ntouched;                     // > kTouchCap means the list overflowed
+    int nrounds;
+    uint32_t ncand[2];                // candidates counted by pass A (alternating super-chunks)
     const uint32_t* slice[kMaxHot];   // bitmap rows of the spectrum's hot slices
     uint32_t slice_inc[kMaxHot];      // counter increment of a set bit
     uint32_t hist[kHistBins];
@@ -125,17 +144,18 @@ struct SearchShared {
     uint32_t wpid[kMaxWarps];
     uint32_t wpk[kMaxWarps];
     uint32_t wsum[kMaxWarps];
+    uint32_t wcand[kMaxWarps];
     int nnorm, nhotc, nslices, nhotpeaks;
     uint64_t unit;
     uint32_t q, np;
     uint32_t seg_lo, seg_hi;
 };
 
-__device__ __forceinline__ uint32_t counter_inc(uint32_t e, uint32_t iq) {
-    return iq + ((e & 1u) ? (1u << kNyShift) : (1u << kNbShift));
+__device__ __forceinline__ uint32_t counter_inc_y(uint32_t isy, uint32_t iq) {
+    return iq + (isy ? (1u << kNyShift) : (1u << kNbShift));
 }
 
-__device__ __forceinline__ uint32_t slot_of(uint32_t off) { return (off * 2654435761u) >> 19; }   // 13 bits
+__device__ __forceinline__ uint32_t slot_of(uint32_t off) { return (off * 2654435761u) >> 22; }   // 10 bits
 
 // Exclusive scan of the ordinary peaks' run lengths, in two halves around a
 // barrier the caller provides.  Thread tid owns peaks tid*ppt .. +ppt-1.
@@ -159,6 +179,14 @@ __device__ __forceinline__ uint32_t scan_runs_1(SearchShared& sh, int nnorm, int
     return incl - sum;
 }
 
+// Warp shares are multiples of 4 entries so that a lane's 4 consecutive
+// entries never cross into the next warp's share.
+template <int THREADS>
+__device__ __forceinline__ uint32_t warp_share(uint32_t total) {
+    constexpr int nwarps = THREADS / 32;
+    return ((total + nwarps - 1) / nwarps + 3) & ~3u;
+}
+
 template <int THREADS, int PPT>
 __device__ __forceinline__ void scan_runs_2(SearchShared& sh, int buf, int nnorm, int ppt, uint32_t excl,
                                             const uint32_t (&ra)[PPT], const uint32_t (&rb)[PPT]) {
@@ -171,7 +199,7 @@ __device__ __forceinline__ void scan_runs_2(SearchShared& sh, int buf, int nnorm
         if (w < warp) wbase += s;
         total += s;
     }
-    const uint32_t per = (total + nwarps - 1) / nwarps;
+    const uint32_t per = warp_share<THREADS>(total);
     uint32_t run = wbase + excl;
 #pragma unroll
     for (int i = 0; i < PPT; ++i) {
@@ -191,20 +219,28 @@ __device__ __forceinline__ void scan_runs_2(SearchShared& sh, int buf, int nnorm
 
 template <int KMAX, int THREADS>
 __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel(SearchArgs a) {
-    extern __shared__ __align__(16) unsigned long long tab[];   // kSlots slots, or 2 * kSlots direct counters
-    uint32_t* const cnt = reinterpret_cast<uint32_t*>(tab);
+    extern __shared__ __align__(16) uint32_t smem32[];   // 16384 words (layout above)
+    uint32_t* const cnt = smem32;
+    uint32_t* const seen = smem32;
+    uint32_t* const twice = smem32 + kPlaneWords;
+    uint32_t* const logw = smem32 + kLogWord;
+    unsigned long long* const tab = reinterpret_cast<unsigned long long*>(smem32 + kSlotWord);
     __shared__ SearchShared sh;
     constexpr int nwarps = THREADS / 32;
     constexpr int PPT = kMaxTopN / THREADS;             // ordinary peaks per thread (at most)
+    constexpr int WPT = kPlaneWords / THREADS;          // plane words per thread
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const uint32_t last_col = a.skip_stride - 1;
-    for (int i = tid; i < (int)kSlots; i += THREADS) tab[i] = 0ull;
+    for (int i = tid; i < (int)kChunk; i += THREADS) smem32[i] = 0u;
     for (int i = tid; i < (int)kHistBins; i += THREADS) sh.hist[i] = 0;
     for (int i = tid; i <= (int)kMaxLen; i += THREADS) sh.lf[i] = a.lf[i];
+    if (tid == 0) { sh.ncand[0] = 0u; sh.ncand[1] = 0u; }
     const uint64_t total_units = a.seg_off[a.n];
     const int k = (int)a.k;
     const uint32_t min_shared = a.min_shared;
+    int par = 0;                  // alternates per super-chunk: which ncand counts
+    uint32_t log_dirty = 0;       // log words that may be non-zero
     __syncthreads();
     for (;;) {
         if (tid == 0) {
@@ -279,6 +315,9 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel
         __syncthreads();
         const int nnorm = sh.nnorm, nslices = sh.nslices;
         const bool hot_alone = sh.nhotpeaks >= (int)min_shared;
+        // peptides hit once are candidates too when the hot slices alone can
+        // supply the other min_shared - 1 shared peaks
+        const bool once_counts = (uint32_t)nslices + 1u >= min_shared;
         const int ppt = (nnorm + THREADS - 1) / THREADS;
         const uint32_t col_lo = seg_lo >> kChunkShift, col_end = ((seg_hi - 1) >> kChunkShift) + 1;
         uint32_t ra[PPT], rb[PPT];
@@ -310,7 +349,8 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel
             for (int w = 0; w < nwarps; ++w) total += sh.wsum[w];
             const uint32_t ncols = col_end - col_lo;
             if (!hot_alone) {
-                uint64_t want = total ? ((uint64_t)a.target_entries * ncols) / total : ncols;
+                const uint32_t target = min(a.target_entries, kMaxEntries);
+                uint64_t want = total ? ((uint64_t)target * ncols) / total : ncols;
                 if (want < 1) want = 1;
                 if (want > kMaxCols) want = kMaxCols;
                 m = min((uint32_t)want, ncols);
@@ -320,72 +360,48 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel
         TopK<KMAX> top;
         top.init();
 
-        // entries of super-chunk [cbase, cbase + span) clipped to [x0, x1);
-        // direct counters when dense, otherwise the hash table
-        auto accumulate = [&](int buf, uint32_t cbase, uint32_t x0, uint32_t x1, bool dense) {
+        // Calls fn(f, entry, peak) for every entry f of parity buffer buf.
+        // Warp w takes a contiguous share; lane l takes f0 + l + 32 j, kJ
+        // loads in flight before any is used.  Each lane walks the runs
+        // forward, keeping the current run's end and the entry-array base
+        // gb (entry f of the run is entry[gb + f]) in registers.
+        auto for_each_entry = [&](int buf, auto&& fn) {
+            constexpr int kJ = 8;
             const uint32_t R = sh.pre[buf][nnorm];
-            const uint32_t per = (R + nwarps - 1) / nwarps;
+            const uint32_t per = warp_share<THREADS>(R);
             const uint32_t f0 = (uint32_t)warp * per, f1 = min(R, f0 + per);
-            int li = 0;
-            if (f0 < f1) {
-                li = sh.wli[buf][warp];
-                const uint32_t fs = f0 + lane;
-                if (fs < f1)
-                    while (sh.pre[buf][li + 1] <= fs) ++li;
-            }
-            for (uint32_t fb = f0; fb < f1; fb += 4 * 32) {   // uniform across the warp
-                uint32_t e[4], inc[4];
+            if (f0 >= f1) return;
+            int li = sh.wli[buf][warp];
+            uint32_t nxt = sh.pre[buf][li + 1];
+            uint64_t gb = sh.pbase[li] + sh.rs[buf][li] - sh.pre[buf][li];
+            for (uint32_t fb = f0 + lane; fb < f1; fb += 32 * kJ) {
+                uint32_t ev[kJ];
+                uint32_t lp[kJ];
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const uint32_t ff = fb + r * 32 + lane;
-                    e[r] = 0xffffffffu;
-                    inc[r] = 0;
-                    if (ff < f1) {
-                        while (sh.pre[buf][li + 1] <= ff) ++li;
-                        e[r] = __ldg(a.entry + sh.pbase[li] + sh.rs[buf][li] + (ff - sh.pre[buf][li]));
-                        inc[r] = sh.pinc[li];
-                    }
-                }
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const uint32_t pid = e[r] >> 1;
-                    const bool act = pid >= x0 && pid < x1;
-                    bool first = false;
-                    uint32_t where = 0;
-                    if (act) {
-                        const uint32_t off = pid - cbase;
-                        const uint32_t v = counter_inc(e[r], inc[r]);
-                        if (dense) {
-                            first = atomicAdd(&cnt[off], v) == 0u;
-                            where = off;
-                        } else {
-                            const unsigned long long item = ((unsigned long long)off << 32) | v;
-                            uint32_t sl = slot_of(off);
-                            for (uint32_t probe = 0; probe < kSlots; ++probe) {
-                                const unsigned long long old = atomicCAS(&tab[sl], 0ull, item);
-                                if (old == 0ull) { first = true; break; }
-                                if ((uint32_t)(old >> 32) == off) { atomicAdd(&tab[sl], (unsigned long long)v); break; }
-                                sl = (sl + 1) & (kSlots - 1);
-                            }
-                            where = sl;
+                for (int j = 0; j < kJ; ++j) {
+                    const uint32_t f = fb + 32 * j;
+                    ev[j] = 0xffffffffu;
+                    lp[j] = 0;
+                    if (f < f1) {
+                        while (f >= nxt) {
+                            ++li;
+                            nxt = sh.pre[buf][li + 1];
+                            gb = sh.pbase[li] + sh.rs[buf][li] - sh.pre[buf][li];
                         }
-                    }
-                    const unsigned bal = __ballot_sync(0xffffffffu, first);
-                    if (bal) {
-                        const int leader = __ffs(bal) - 1;
-                        int base = 0;
-                        if (lane == leader) base = atomicAdd(&sh.ntouched, __popc(bal));
-                        base = __shfl_sync(0xffffffffu, base, leader);
-                        const int slot = base + __popc(bal & lt);
-                        if (first && slot < kTouchCap) sh.touched[slot] = (uint16_t)where;
+                        lp[j] = (uint32_t)li;
+                        ev[j] = __ldg(a.entry + (gb + f));
                     }
                 }
+#pragma unroll
+                for (int j = 0; j < kJ; ++j)
+                    if (fb + 32 * j < f1) fn(fb + 32 * j, ev[j], (int)lp[j]);
             }
         };
         auto score = [&](uint32_t c, uint32_t pid) {
             const uint32_t nb = c >> kNbShift, ny = (c >> kNyShift) & 63u;
             if (nb + ny >= min_shared) {
-                const uint32_t S = c & kSMask;
+                uint32_t S = c & kSMask;
+                if (S > a.s_max) S = a.s_max;   // unreachable for a consistent index
                 const int64_t K = sh.lf[nb] + sh.lf[ny] + __ldg(a.ls + S);
                 const int64_t hb = K >> 31;
                 atomicAdd(&sh.hist[hb > 255 ? 255 : (hb < 0 ? 0 : hb)], 1u);
@@ -400,34 +416,37 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel
                 if ((__ldg(sh.slice[s] + (pid >> 5)) >> (pid & 31)) & 1u) c += sh.slice_inc[s];
             score(c, pid);
         };
-        // epilogue of a super-chunk; clears what it visits
-        auto epilogue = [&](uint32_t cbase, uint32_t x0, uint32_t x1, bool dense) {
+
+        // ---- one column with direct counters (the caller provides the
+        // barriers before and after)
+        auto column_pass = [&](int buf, uint32_t cb, uint32_t x0, uint32_t x1) {
+            for_each_entry(buf, [&](uint32_t, uint32_t e, int li) {
+                const uint32_t pid = e >> 1;
+                bool first = false;
+                uint32_t off = 0;
+                if (pid >= x0 && pid < x1) {
+                    off = pid - cb;
+                    first = atomicAdd(&cnt[off], counter_inc_y(e & 1u, sh.pinc[li])) == 0u;
+                }
+                if (first) {
+                    const int slot = atomicAdd(&sh.ntouched, 1);
+                    if (slot < kTouchCap) sh.touched[slot] = (uint16_t)off;
+                }
+            });
+            __syncthreads();
             const int nt = sh.ntouched;
             if (nt <= kTouchCap && !hot_alone) {
                 for (int i = tid; i < nt; i += THREADS) {
                     const uint32_t w = sh.touched[i];
-                    if (dense) {
-                        const uint32_t c = cnt[w];
-                        cnt[w] = 0u;
-                        visit(c, cbase + w);
-                    } else {
-                        const unsigned long long v = tab[w];
-                        tab[w] = 0ull;
-                        visit((uint32_t)v, cbase + (uint32_t)(v >> 32));
-                    }
-                }
-            } else if (!dense) {
-                for (uint32_t i = tid; i < kSlots; i += THREADS) {
-                    const unsigned long long v = tab[i];
-                    if (v == 0ull) continue;
-                    tab[i] = 0ull;
-                    visit((uint32_t)v, cbase + (uint32_t)(v >> 32));
+                    const uint32_t c = cnt[w];
+                    cnt[w] = 0u;
+                    visit(c, cb + w);
                 }
             } else {
-                // every counter of the column, 32 peptide ids per step; with
-                // >= min_shared hot peaks the bitmaps alone can qualify a peptide
+                // every counter, 32 peptide ids per step; bitmaps alone can
+                // qualify a peptide when hot_alone
                 for (uint32_t gi = tid; gi < kChunk / 32; gi += THREADS) {
-                    const uint32_t gp = cbase + (gi << 5);
+                    const uint32_t gp = cb + (gi << 5);
                     if (gp + 32 <= x0 || gp >= x1) continue;
                     const uint32_t lo_b = x0 > gp ? x0 - gp : 0u;
                     const uint32_t hi_b = x1 - gp >= 32u ? 32u : x1 - gp;
@@ -459,6 +478,140 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel
                     for (int j = 0; j < 32; ++j) cnt[(gi << 5) + ((j + lane) & 31)] = 0u;
                 }
             }
+            __syncthreads();
+            if (tid == 0) sh.ntouched = 0;
+        };
+
+        // ---- a super-chunk in passes (see the header); entries of parity
+        // buffer buf, peptide ids [x0, x1) of the span starting at cb
+        auto pass_a = [&](int buf, uint32_t cb, uint32_t x0, uint32_t x1, int par) {
+            uint32_t fresh = 0;   // twice bits this lane set first
+            for_each_entry(buf, [&](uint32_t f, uint32_t e, int li) {
+                const uint32_t pid = e >> 1;
+                uint32_t rec = 0xffffffffu;
+                if (pid >= x0 && pid < x1) {
+                    const uint32_t off = pid - cb;
+                    const uint32_t bit = 1u << (off & 31);
+                    if (atomicOr(&seen[off >> 5], bit) & bit)
+                        fresh += (atomicOr(&twice[off >> 5], bit) & bit) ? 0u : 1u;
+                    rec = off | ((e & 1u) << 17) | ((uint32_t)li << 18);
+                }
+                logw[f] = rec;
+            });
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) fresh += __shfl_xor_sync(0xffffffffu, fresh, o);
+            if (lane == 0 && fresh) atomicAdd(&sh.ncand[par], fresh);
+        };
+        // candidate plane (twice, plus peptides seen once with enough hot
+        // bits when once_counts), its count and the rounds; clears the seen
+        // plane.  Warp w owns words [w * wpw, (w + 1) * wpw), lane l every
+        // 32nd of them (barriers inside).
+        auto mark = [&](uint32_t cb, uint32_t words) {
+            const uint32_t wpw = words / nwarps;   // a multiple of 32
+            const uint32_t wbeg = (uint32_t)warp * wpw;
+            uint32_t mine = 0;
+            for (uint32_t i = lane; i < wpw; i += 32) {
+                const uint32_t w = wbeg + i;
+                const uint32_t s1 = seen[w];
+                uint32_t c2 = twice[w];
+                if (s1) {
+                    seen[w] = 0u;
+                    if (once_counts) {
+                        uint32_t b1 = 0, b2 = 0, b3 = 0;   // hot-bit count per peptide: b3 marks 4 or more
+                        for (int s = 0; s < nslices; ++s) {
+                            const uint32_t h = __ldg(sh.slice[s] + (cb >> 5) + w);
+                            const uint32_t k1 = b1 & h;
+                            b1 ^= h;
+                            const uint32_t k2 = b2 & k1;
+                            b2 ^= k1;
+                            b3 |= k2;
+                        }
+                        const uint32_t need = min_shared - 1;   // <= nslices <= kMaxHot
+                        uint32_t enough;
+                        if (need == 0) enough = 0xffffffffu;
+                        else if (need == 1) enough = b1 | b2 | b3;
+                        else if (need == 2) enough = b2 | b3;
+                        else if (need == 3) enough = (b2 & b1) | b3;
+                        else enough = b3;                        // a superset: visit() is exact
+                        c2 |= s1 & enough;
+                        twice[w] = c2;
+                    }
+                }
+                mine += __popc(c2);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+            if (lane == 0) sh.wcand[warp] = mine;
+            // a round whose first word is never found is empty: it starts at words
+            for (int r = tid; r <= (int)kMaxRounds; r += THREADS) sh.wb[r] = r == 0 ? 0 : (uint16_t)words;
+            __syncthreads();
+            uint32_t run = 0, total = 0;
+#pragma unroll
+            for (int w = 0; w < nwarps; ++w) {
+                if (w < warp) run += sh.wcand[w];
+                total += sh.wcand[w];
+            }
+            // round r holds the words with r * kRound <= candidates-before < (r + 1) * kRound
+            for (uint32_t i0 = 0; i0 < wpw; i0 += 32) {
+                const uint32_t w = wbeg + i0 + lane;
+                const uint32_t cw = __popc(twice[w]);
+                uint32_t incl = cw;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t x = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += x;
+                }
+                const uint32_t before = run + incl - cw;
+                const uint32_t r = before / kRound;
+                if (r > 0 && (before - __popc(twice[w - 1])) / kRound < r) sh.wb[r] = (uint16_t)w;
+                run += __shfl_sync(0xffffffffu, incl, 31);
+            }
+            if (tid == 0) sh.nrounds = (int)(total ? (total - 1) / kRound + 1 : 0);
+            __syncthreads();
+        };
+        auto replay = [&](uint32_t R, uint32_t wlo, uint32_t whi) {
+            for (uint32_t i = tid; i < R; i += THREADS) {
+                const uint32_t rec = logw[i];
+                if (rec == 0xffffffffu) continue;
+                const uint32_t off = rec & 0x1ffffu;
+                const uint32_t w = off >> 5;
+                if (!((twice[w] >> (off & 31)) & 1u) || w < wlo || w >= whi) continue;
+                const uint32_t v = counter_inc_y((rec >> 17) & 1u, sh.pinc[rec >> 18]);
+                const unsigned long long item = ((unsigned long long)off << 32) | v;
+                uint32_t sl = slot_of(off);
+                for (uint32_t probe = 0; probe < kSlots; ++probe) {
+                    const unsigned long long old = atomicCAS(&tab[sl], 0ull, item);
+                    if (old == 0ull) break;
+                    if ((uint32_t)(old >> 32) == off) { atomicAdd(&tab[sl], (unsigned long long)v); break; }
+                    sl = (sl + 1) & (kSlots - 1);
+                }
+            }
+        };
+        auto slots_epilogue = [&](uint32_t cb) {
+            for (uint32_t i = tid; i < kSlots; i += THREADS) {
+                const unsigned long long v = tab[i];
+                if (v == 0ull) continue;
+                tab[i] = 0ull;
+                visit((uint32_t)v, cb + (uint32_t)(v >> 32));
+            }
+        };
+        auto clear_words = [&](uint32_t* plane, uint32_t words) {
+            uint4* p4 = reinterpret_cast<uint4*>(plane);
+            for (uint32_t i = tid; i < words / 4; i += THREADS) p4[i] = make_uint4(0u, 0u, 0u, 0u);
+        };
+        // L2 prefetch of this thread's runs [ra, rb) (the next super-chunk's)
+        auto prefetch_runs = [&]() {
+#pragma unroll
+            for (int i = 0; i < PPT; ++i) {
+                const int t = tid * ppt + i;
+                if (i < ppt && t < nnorm && rb[i] > ra[i]) {
+                    const uint32_t* p0 = a.entry + sh.pbase[t] + ra[i];
+                    const uint64_t s0 = reinterpret_cast<uint64_t>(p0) & ~uint64_t(15);
+                    const uint64_t s1 = (reinterpret_cast<uint64_t>(p0 + (rb[i] - ra[i])) + 15) & ~uint64_t(15);
+                    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(s0), "r"((uint32_t)(s1 - s0))
+                                 : "memory");
+                }
+            }
         };
 
         // prologue: bounds of the first super-chunk
@@ -474,22 +627,28 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel
         __syncthreads();
         while (c < col_end) {
             const uint32_t R = sh.pre[buf][nnorm];
-            if (R > kMaxEntries && e - c > 1) {
-                // too many entries for the table: this super-chunk column by column
-                for (uint32_t cc = c; cc < e; ++cc) {
-                    load_runs(cc, cc + 1);
-                    const uint32_t excl = scan_runs_1<PPT>(sh, nnorm, ppt, ra, rb);
+            if (hot_alone || R > kMaxEntries) {
+                // column by column with direct counters, which cover the log
+                if (log_dirty) {
+                    for (uint32_t i = tid; i < log_dirty; i += THREADS) logw[i] = 0u;
+                    log_dirty = 0;
                     __syncthreads();
-                    scan_runs_2<THREADS, PPT>(sh, buf ^ 1, nnorm, ppt, excl, ra, rb);
+                }
+                if (e - c == 1) {
+                    const uint32_t cb = c << kChunkShift;
+                    column_pass(buf, cb, max(seg_lo, cb), min(seg_hi, cb + kChunk));
                     __syncthreads();
-                    const uint32_t cb = cc << kChunkShift;
-                    const uint32_t x0 = max(seg_lo, cb), x1 = min(seg_hi, cb + kChunk);
-                    accumulate(buf ^ 1, cb, x0, x1, true);
-                    __syncthreads();
-                    epilogue(cb, x0, x1, true);
-                    __syncthreads();
-                    if (tid == 0) sh.ntouched = 0;
-                    __syncthreads();
+                } else {
+                    for (uint32_t cc = c; cc < e; ++cc) {
+                        load_runs(cc, cc + 1);
+                        const uint32_t excl = scan_runs_1<PPT>(sh, nnorm, ppt, ra, rb);
+                        __syncthreads();
+                        scan_runs_2<THREADS, PPT>(sh, buf ^ 1, nnorm, ppt, excl, ra, rb);
+                        __syncthreads();
+                        const uint32_t cb = cc << kChunkShift;
+                        column_pass(buf ^ 1, cb, max(seg_lo, cb), min(seg_hi, cb + kChunk));
+                        __syncthreads();
+                    }
                 }
                 c = e;
                 if (c < col_end) {
@@ -502,24 +661,48 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel
                 }
                 continue;
             }
-            const bool dense = (e - c) == 1;
             const uint32_t cbase = c << kChunkShift;
             const uint32_t x0 = max(seg_lo, cbase), x1 = min(seg_hi, e << kChunkShift);
+            const uint32_t words = ((e - c) << kChunkShift) >> 5;
             const uint32_t nc = e, ne = min(e + m, col_end);
             const bool more = nc < col_end;
-            if (more) load_runs(nc, ne);                 // next super-chunk's bounds
-            accumulate(buf, cbase, x0, x1, dense);
+            if (more) {                                   // next super-chunk's bounds, into L2
+                load_runs(nc, ne);
+                prefetch_runs();
+            }
+            pass_a(buf, cbase, x0, x1, par);
             uint32_t excl = 0;
             if (more) excl = scan_runs_1<PPT>(sh, nnorm, ppt, ra, rb);
+            if (R > log_dirty) log_dirty = R;
             __syncthreads();
-            epilogue(cbase, x0, x1, dense);
+            const uint32_t ncand = sh.ncand[par];
+            if (tid == 0) sh.ncand[par ^ 1] = 0u;         // the next super-chunk's count
+            if (once_counts || ncand > kRound) {
+                mark(cbase, words);                       // two barriers inside
+                const int nr = sh.nrounds;
+                for (int r = 0; r < nr; ++r) {
+                    const uint32_t wlo = sh.wb[r];
+                    const uint32_t whi = r == nr - 1 ? words : sh.wb[r + 1];
+                    replay(R, wlo, whi);
+                    __syncthreads();
+                    slots_epilogue(cbase);
+                    __syncthreads();
+                }
+                clear_words(twice, words);
+            } else if (ncand) {
+                replay(R, 0u, words);
+                __syncthreads();
+                slots_epilogue(cbase);
+                clear_words(seen, words);
+                clear_words(twice, words);
+            } else {
+                clear_words(seen, words);                 // the twice plane is empty
+            }
             if (more) scan_runs_2<THREADS, PPT>(sh, buf ^ 1, nnorm, ppt, excl, ra, rb);
-            __syncthreads();
-            if (tid == 0) sh.ntouched = 0;
             buf ^= 1;
+            par ^= 1;
             c = nc;
             e = ne;
-            // the next accumulate appends to ntouched: make the reset visible
             __syncthreads();
         }
         // block top-k: k rounds of block-wide argmax over the thread heads
