@@ -174,6 +174,33 @@ hicops_status hicops_build_index(const hicops_proteins* proteins, const hicops_m
 hicops_status hicops_search(hicops_index* index, const hicops_batch* batch, hicops_psm* out_psm,
                             uint32_t* out_hist, uint32_t* out_nscored);
 
+/* Largest batch hicops_search_noalloc accepts. */
+#define HICOPS_NOALLOC_MAX_SPECTRA 64u
+
+/* hicops_search without any device or host allocation.  The paper has no
+ * counterpart: it is an addition of this library for callers that must not
+ * allocate while they search, e.g. a serving loop with hard latency bounds
+ * (cudaFree synchronises the device and cudaMalloc can stall on it) or a
+ * process whose device memory is already reserved by another allocator, so
+ * that hicops_search's stream-ordered scratch would fail.
+ *   Same search, results and output layout as hicops_search, for a batch of
+ * at most HICOPS_NOALLOC_MAX_SPECTRA spectra whose buffers are all on the
+ * device (batch->on_device = 1).  out_psm [n * top_k] is a device buffer;
+ * out_hist [n * 256] and out_nscored [n] are device buffers or NULL.  Work is
+ * enqueued on batch->cuda_stream and the call returns without waiting.
+ *   Scratch: one fixed array of about 1.2 MB in the library's device memory
+ * per device, shared by every call on that device; each call rewrites what it
+ * uses, so nothing has to be cleared between calls.  Calls whose work
+ * overlaps in time (other streams or threads) race on that array and give
+ * wrong results: order them, e.g. on one stream.  The first call on each
+ * device looks up the array's device address (which may load the library's
+ * device code on that device); make that first call before any stream
+ * capture begins.
+ * Errors: HICOPS_EINVAL (more than HICOPS_NOALLOC_MAX_SPECTRA spectra, host
+ * pointers, the hicops_search cases), HICOPS_ECUDA. */
+hicops_status hicops_search_noalloc(hicops_index* index, const hicops_batch* batch, hicops_psm* out_psm,
+                                    uint32_t* out_hist, uint32_t* out_nscored);
+
 /* Measurement helper: per spectrum, the precursor window [lo, hi), the
  * number of retained peaks and the number of index entries inside the window
  * over the retained peaks' buckets (H(q), the work of filter_2).  Any output

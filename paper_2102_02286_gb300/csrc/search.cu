@@ -14,6 +14,7 @@
 // (hicops_plan_*) allocates it once and can replay the sequence as a CUDA
 // graph.
 #include <atomic>
+#include <mutex>
 #include <cfloat>
 #include <cmath>
 #include <vector>
@@ -524,4 +525,108 @@ extern "C" hicops_status hicops_index_last_timing(hicops_index* idx, hicops_timi
     out->merge_ms = t[3];
     HC_CUDA(cudaEventElapsedTime(&out->total_ms, e[0], e[4]));
     return HICOPS_OK;
+}
+
+// ---- search without allocation (an addition of this library; the paper has
+// no counterpart).  The scratch of one search of at most
+// HICOPS_NOALLOC_MAX_SPECTRA spectra lives in one file-scope device array;
+// the entry point carves the same Workspace out of it that hicops_search
+// allocates, and runs the same kernel sequence.
+namespace hicops {
+namespace {
+
+constexpr uint32_t kNoAllocSegs = 16;      // work units per spectrum at most
+constexpr int kNoAllocDevices = 64;        // device ordinals served
+constexpr uint64_t align256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
+
+// Workspace bytes for cap spectra at the largest top_n_peaks and top_k, in
+// alloc_workspace's order (each piece 256-byte aligned), plus room for the
+// scan's temporary words.
+constexpr uint64_t noalloc_bytes(uint64_t cap) {
+    return 2 * align256(4 * cap * kMaxTopN)                      // qbin, qiq
+           + 4 * align256(4 * cap)                               // qn, lo, hi, nseg
+           + align256(8 * (cap + 1))                             // seg_off
+           + 4096                                                // scan temporaries
+           + align256(sizeof(UnitTop) * cap * kNoAllocSegs * kMaxTopK)
+           + 256                                                 // work counter
+           + align256(sizeof(hicops_psm) * cap * kMaxTopK)       // psm (unused here)
+           + align256(4 * cap * kHistBins) + align256(4 * cap);  // hist, n_scored
+}
+constexpr uint64_t kNoAllocBytes = noalloc_bytes(HICOPS_NOALLOC_MAX_SPECTRA);
+static_assert(kNoAllocBytes <= (2u << 20), "the no-allocation scratch is meant to stay small");
+
+// Shared by every hicops_search_noalloc call on a device.  Nothing in it
+// has to start at zero: each search writes its pieces before reading them
+// and clears the histogram, counters and work counter itself.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_base[kNoAllocDevices] = {};
+
+// Device address of the array on device dev, which must be current.  The
+// first call on a device looks it up (this can load the module on that
+// device).
+hicops_status noalloc_scratch(int dev, unsigned char** out) {
+    if (dev < 0 || dev >= kNoAllocDevices) {
+        set_error("hicops_search_noalloc serves device ordinals below %d, not %d", kNoAllocDevices, dev);
+        return HICOPS_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_base[dev]) {
+        void* p = nullptr;
+        HC_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_base[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(g_noalloc_base[dev]);
+    return HICOPS_OK;
+}
+
+// alloc_workspace's allocator over the fixed array: hands out consecutive
+// 256-byte aligned pieces and fails when they would not fit.
+struct Carve {
+    unsigned char* base;
+    uint64_t cap, used;
+    template <class T>
+    cudaError_t get(T** p, uint64_t n) {
+        const uint64_t bytes = align256(sizeof(T) * (n ? n : 1));
+        if (used + bytes > cap) return cudaErrorMemoryAllocation;
+        *p = reinterpret_cast<T*>(base + used);
+        used += bytes;
+        return cudaSuccess;
+    }
+};
+
+}  // namespace
+}  // namespace hicops
+
+extern "C" hicops_status hicops_search_noalloc(hicops_index* idx, const hicops_batch* b, hicops_psm* out_psm,
+                                               uint32_t* out_hist, uint32_t* out_nscored) {
+    hicops_status st = check_batch(idx, b);
+    if (st != HICOPS_OK) return st;
+    if (!b->on_device || !out_psm) {
+        set_error("hicops_search_noalloc takes device pointers (on_device = 1) and a device out_psm");
+        return HICOPS_EINVAL;
+    }
+    const uint32_t n = b->n;
+    if (n > HICOPS_NOALLOC_MAX_SPECTRA) {
+        set_error("batch of %u spectra exceeds hicops_search_noalloc's limit of %u (HICOPS_NOALLOC_MAX_SPECTRA)", n,
+                  (unsigned)HICOPS_NOALLOC_MAX_SPECTRA);
+        return HICOPS_EINVAL;
+    }
+    if (n == 0) return HICOPS_OK;
+    unsigned char* base = nullptr;
+    st = noalloc_scratch(idx->dev.device, &base);
+    if (st != HICOPS_OK) return st;
+    Carve cv{base, kNoAllocBytes, 0};
+    Workspace w;
+    uint32_t segs = max_segments(idx->dev.cfg, n);
+    if (segs > kNoAllocSegs) segs = kNoAllocSegs;
+    st = alloc_workspace(cv, idx->p, n, segs, true, w);
+    if (st != HICOPS_OK) {
+        set_error("hicops_search_noalloc: scratch of %llu bytes is too small", (unsigned long long)kNoAllocBytes);
+        return HICOPS_ENOMEM;
+    }
+    const DevBatch d{b->peak_off, b->mz, b->intensity, b->prec_mz, b->charge, b->prec_tol_da};
+    return enqueue_search(idx, d, n, w, idx->dev.cfg, out_psm, out_hist ? out_hist : w.hist,
+                          out_nscored ? out_nscored : w.ns, (cudaStream_t)b->cuda_stream, false);
 }

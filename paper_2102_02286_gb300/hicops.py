@@ -116,6 +116,7 @@ def load(build_if_missing: bool = False):
         "hicops_index_upload": (st, [P]),
         "hicops_build_index": (st, [C.POINTER(Proteins), P, C.c_uint32, C.POINTER(Params), C.POINTER(P)]),
         "hicops_search": (st, [P, C.POINTER(Batch), P, P, P]),
+        "hicops_search_noalloc": (st, [P, C.POINTER(Batch), P, P, P]),
         "hicops_search_work": (st, [P, C.POINTER(Batch), P, P, P, P]),
         "hicops_index_set_config": (st, [P, C.POINTER(SearchConfig)]),
         "hicops_autotune": (st, [P, C.POINTER(Batch), C.POINTER(SearchConfig), C.POINTER(C.c_double)]),
@@ -289,6 +290,13 @@ class Index:
         _check(load().hicops_search(self.h, C.byref(b), out.psm.data_ptr(),
                                     out.hist.data_ptr() if out.hist is not None else None,
                                     out.n_scored.data_ptr() if out.n_scored is not None else None))
+
+    def search_noalloc(self, dev_batch: "DeviceBatch", out: "DeviceResult", stream=None):
+        """hicops_search_noalloc: device tensors, at most NOALLOC_MAX_SPECTRA spectra, no allocation."""
+        b = _device_batch_struct(dev_batch, stream)
+        _check(load().hicops_search_noalloc(self.h, C.byref(b), out.psm.data_ptr(),
+                                            out.hist.data_ptr() if out.hist is not None else None,
+                                            out.n_scored.data_ptr() if out.n_scored is not None else None))
 
 
 def _device_batch_struct(dev_batch, stream=None) -> Batch:
