@@ -88,13 +88,18 @@ struct TopK {
     uint32_t pid[KMAX];
     uint32_t pk[KMAX];
     int n;
+    int64_t tkey;     // the k-th entry while the list is full
+    uint32_t tpid;
     __device__ __forceinline__ void init() {
         n = 0;
+        tkey = INT64_MIN;
+        tpid = 0xffffffffu;
 #pragma unroll
         for (int i = 0; i < KMAX; ++i) { key[i] = INT64_MIN; pid[i] = 0xffffffffu; pk[i] = 0; }
     }
     // sorted by (key desc, pid asc); keeps the best k
     __device__ __forceinline__ void insert(int64_t kk, uint32_t p, uint32_t packed, int k) {
+        if (n == k && !(kk > tkey || (kk == tkey && p < tpid))) return;   // not among the best k
         int pos = 0;
 #pragma unroll
         for (int i = 0; i < KMAX; ++i)
@@ -107,6 +112,15 @@ struct TopK {
         for (int i = 0; i < KMAX; ++i)
             if (i == pos) { key[i] = kk; pid[i] = p; pk[i] = packed; }
         if (n < k) ++n;
+        if (n == k) {   // the worst of the first k
+            int64_t tk = INT64_MAX;
+            uint32_t tp = 0u;
+#pragma unroll
+            for (int i = 0; i < KMAX; ++i)
+                if (i < k && (key[i] < tk || (key[i] == tk && pid[i] > tp))) { tk = key[i]; tp = pid[i]; }
+            tkey = tk;
+            tpid = tp;
+        }
     }
     __device__ __forceinline__ void pop() {
 #pragma unroll
@@ -587,17 +601,37 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel
                 }
             }
         };
+        // Visits the occupied slots.  Warp w compacts the occupied slot
+        // indices of its share [w * spw, (w + 1) * spw) into the same words
+        // of the seen plane (free once pass A is over), visits them with all
+        // lanes, and zeroes the slots and those plane words.
         auto slots_epilogue = [&](uint32_t cb) {
-            for (uint32_t i = tid; i < kSlots; i += THREADS) {
-                const unsigned long long v = tab[i];
-                if (v == 0ull) continue;
-                tab[i] = 0ull;
+            constexpr uint32_t spw = kSlots / nwarps;
+            const uint32_t base = (uint32_t)warp * spw;
+            uint32_t cnt = 0;
+#pragma unroll
+            for (uint32_t i0 = 0; i0 < spw; i0 += 32) {
+                const uint32_t sl = base + i0 + lane;
+                const bool occ = tab[sl] != 0ull;
+                const unsigned msk = __ballot_sync(0xffffffffu, occ);
+                if (occ) seen[base + cnt + __popc(msk & lt)] = sl;
+                cnt += __popc(msk);
+            }
+            __syncwarp();
+            for (uint32_t i = lane; i < cnt; i += 32) {
+                const uint32_t sl = seen[base + i];
+                const unsigned long long v = tab[sl];
+                tab[sl] = 0ull;
                 visit((uint32_t)v, cb + (uint32_t)(v >> 32));
             }
+            __syncwarp();
+#pragma unroll
+            for (uint32_t i0 = 0; i0 < spw; i0 += 32) seen[base + i0 + lane] = 0u;
         };
-        auto clear_words = [&](uint32_t* plane, uint32_t words) {
+        // zeroes plane words [w0, w1), both multiples of 4
+        auto clear_words = [&](uint32_t* plane, uint32_t w0, uint32_t w1) {
             uint4* p4 = reinterpret_cast<uint4*>(plane);
-            for (uint32_t i = tid; i < words / 4; i += THREADS) p4[i] = make_uint4(0u, 0u, 0u, 0u);
+            for (uint32_t i = w0 / 4 + tid; i < w1 / 4; i += THREADS) p4[i] = make_uint4(0u, 0u, 0u, 0u);
         };
         // L2 prefetch of this thread's runs [ra, rb) (the next super-chunk's)
         auto prefetch_runs = [&]() {
@@ -688,15 +722,15 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel
                     slots_epilogue(cbase);
                     __syncthreads();
                 }
-                clear_words(twice, words);
+                clear_words(twice, 0u, words);
             } else if (ncand) {
                 replay(R, 0u, words);
                 __syncthreads();
-                slots_epilogue(cbase);
-                clear_words(seen, words);
-                clear_words(twice, words);
+                slots_epilogue(cbase);                    // zeroes seen words [0, kSlots)
+                clear_words(seen, kSlots, words);
+                clear_words(twice, 0u, words);
             } else {
-                clear_words(seen, words);                 // the twice plane is empty
+                clear_words(seen, 0u, words);             // the twice plane is empty
             }
             if (more) scan_runs_2<THREADS, PPT>(sh, buf ^ 1, nnorm, ppt, excl, ra, rb);
             buf ^= 1;
