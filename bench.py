@@ -47,6 +47,16 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--tune-spectra", type=int, default=20000, help="autotuner sample (0 = default shape)")
+    ap.add_argument("--mode", default="step", choices=["step", "batched", "serving"],
+                    help="step: the headline search step; batched: one autotuned graph-replayed launch over "
+                         "an uneven batch against plain per-class launches; serving: Poisson request stream "
+                         "through the continuous-batching server against a one-batch-per-launch loop")
+    ap.add_argument("--loads", default="10000,30000,100000,300000,1000000,2000000",
+                    help="serving: offered loads in spectra/s")
+    ap.add_argument("--load-seconds", type=float, default=3.0, help="serving: arrival window per load")
+    ap.add_argument("--load-spectra", type=int, default=300000, help="serving: cap on spectra per load")
+    ap.add_argument("--shape", default="", help="fixed launch shape threads,chunk_entries,ctas_per_sm,seg_pids "
+                                                "(skips the autotuner)")
     return ap.parse_args()
 
 
@@ -133,11 +143,18 @@ def search_traffic_record():
         return None
     with open(p) as f:
         rec = json.load(f)
-    src = os.path.join(ROOT, "paper_2102_02286_gb300", "csrc", "search.cu")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if rec.get("search_cu_sha256") != h or rec.get("workload") is None:
+    if rec.get("search_src_sha256") != search_source_hash() or rec.get("workload") is None:
         return None
     return rec
+
+
+def search_source_hash() -> str:
+    """sha256 over the search kernel's sources (the host side and the kernels)."""
+    h = hashlib.sha256()
+    for name in ("search.cu", "search_kernels.cuh", "search_kernel.cuh"):
+        with open(os.path.join(ROOT, "paper_2102_02286_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def cpu_baseline(w, prot, spec, n_sample: int):
@@ -186,10 +203,264 @@ def run_reference(args):
     return 0
 
 
+def spectrum_classes(spec, n_deciles=10):
+    """Plain per-class grouping of a batch: precursor-tolerance class x
+    raw-peak-count decile, each class in batch order."""
+    npk = np.diff(spec.peak_off.astype(np.int64))
+    edges = np.quantile(npk, np.linspace(0, 1, n_deciles + 1)[1:-1])
+    dec = np.searchsorted(edges, npk, side="right")
+    tols = np.unique(spec.tol_da)
+    tcls = np.searchsorted(tols, spec.tol_da)
+    cls = tcls * n_deciles + dec
+    return [np.flatnonzero(cls == c) for c in range(len(tols) * n_deciles) if np.any(cls == c)]
+
+
+def run_batched(args):
+    """Batched form: the whole uneven batch in one persistent launch with the
+    autotuned shape, replayed as a CUDA graph, against one plain hicops_search
+    launch per spectrum class with the default shape; results must be
+    identical."""
+    import torch
+    from paper_2102_02286_gb300 import build as pkg_build
+    from paper_2102_02286_gb300 import hicops as hc
+
+    torch.cuda.set_device(0)
+    pkg_build.build()
+    hc.load()
+    if args.workload == "open_medium":
+        args.workload = "uneven_batched"
+    w = workload(args)
+    prot = synth.make_proteome(w.n_proteins, w.seed, w.protein_len)
+    spec = synth.make_spectra(prot, w)
+    idx = hc.Index(prot.seq, prot.off, w.mods, w.params)
+    n, k = spec.n, w.params.top_k
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    groups = spectrum_classes(spec)
+    sub = [spec.subset(g) for g in groups]
+    dbs = [hc.DeviceBatch.from_spectra(x) for x in sub]
+    outs = [hc.DeviceResult.alloc(x.n, k) for x in sub]
+    db_all = hc.DeviceBatch.from_spectra(spec)
+    out_all = hc.DeviceResult.alloc(n, k)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    # plain per-class launches, default shape
+    idx.set_config(None)
+    launches0 = hc.kernel_launches()
+    per_class_ms = timed(lambda: [idx.search_device(d, o, stream) for d, o in zip(dbs, outs)])
+    per_class_launches = (hc.kernel_launches() - launches0) // (args.warmup + args.steps)
+    # one launch, default shape, no graph
+    plan0 = idx.plan(n, hc.SearchConfig())
+    one_default_ms = timed(lambda: plan0.search(db_all, out_all, stream, graph=False))
+    plan0.close()
+    # one launch, autotuned shape, captured once and replayed as a CUDA graph
+    t0 = time.perf_counter()
+    tune = hc.DeviceBatch.from_spectra(spec.subset(np.arange(min(n, args.tune_spectra or 20000))))
+    shape, _ = idx.autotune(tune)
+    t_tune = time.perf_counter() - t0
+    del tune
+    plan = idx.plan(n, shape)
+    plan.search(db_all, out_all, stream, graph=True)     # capture
+    torch.cuda.synchronize()
+    launches0 = hc.kernel_launches()
+    batched_ms = timed(lambda: plan.search(db_all, out_all, stream, graph=True))
+    batched_launches = (hc.kernel_launches() - launches0) // (args.warmup + args.steps)
+
+    # identical results: every class's rows against the same spectra's rows of the one launch
+    got = out_all.to_host(n, k)
+    identical = True
+    for g, o, x in zip(groups, outs, sub):
+        r = o.to_host(x.n, k)
+        exp = got.psm[g].copy()
+        exp["query"] = np.arange(x.n)[:, None]
+        identical &= bool(np.array_equal(r.psm, exp) and np.array_equal(r.hist, got.hist[g])
+                          and np.array_equal(r.n_scored, got.n_scored[g]))
+    plan.close()
+    idx.close()
+    npk = np.diff(spec.peak_off.astype(np.int64))
+    line = {
+        "metric": "spectra/s, uneven batch: one autotuned persistent launch replayed as a CUDA graph",
+        "value": n / (batched_ms / 1000.0),
+        "unit": "spectra/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": batched_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": workload_desc(w), "spectra_per_step": n,
+                   "peaks_per_spectrum": [int(npk.min()), int(npk.max())],
+                   "tolerances_da": sorted(set(float(t) for t in spec.tol_da)),
+                   "l2": "L2 flushed (256 MB write) before every timed step",
+                   "launch_shape": shape.as_dict(), "autotune_s": t_tune},
+        "baselines": {
+            "per_class_default": {"spectra_per_s": n / (per_class_ms / 1000.0), "ms_per_step": per_class_ms,
+                                  "classes": len(groups), "gpu_launches_per_step": int(per_class_launches),
+                                  "what": "one hicops_search per (tolerance class x peak-count decile), "
+                                          "default shape, stream-ordered scratch per call"},
+            "one_launch_default": {"spectra_per_s": n / (one_default_ms / 1000.0), "ms_per_step": one_default_ms,
+                                   "what": "one plan launch over the whole batch, default shape, no graph"},
+        },
+        "speedup_vs_per_class": per_class_ms / batched_ms,
+        "identical_results": identical,
+        "gpu_launches": int(batched_launches),
+    }
+    print(json.dumps(line), flush=True)
+    return 0 if identical else 1
+
+
+def poisson_requests(rng, offered, seconds, cap_spectra, pool_n, max_batch=4096):
+    """Arrival times (s) and (start, size) slices of the spectrum pool for a
+    Poisson stream of batches with log-uniform sizes in [1, max_batch]."""
+    mean_size = (max_batch - 1) / np.log(max_batch)
+    rate = offered / mean_size                       # requests per second
+    t, total, out = 0.0, 0, []
+    start = int(rng.integers(pool_n))
+    while t < seconds and total < cap_spectra:
+        t += float(rng.exponential(1.0 / rate))
+        size = int(np.clip(np.floor(np.exp(rng.uniform(0.0, np.log(max_batch + 1)))), 1, max_batch))
+        out.append((t, start % pool_n, size))
+        start += size
+        total += size
+    return out
+
+
+def request_batches(spec, reqs):
+    """Host batches for the requests (taken cyclically from the pool)."""
+    out = []
+    for _, st, size in reqs:
+        sel = (np.arange(size) + st) % spec.n
+        out.append(spec.subset(sel))
+    return out
+
+
+def serve_stream(idx, hc, reqs, batches, server):
+    """Replays the arrivals in real time; returns per-request latencies (s),
+    the makespan (s) and the results."""
+    import queue
+    lat = [None] * len(reqs)
+    res = [None] * len(reqs)
+    t0 = time.perf_counter() + 0.05
+    if server is not None:
+        tickets = queue.Queue()
+
+        def collect():
+            for _ in range(len(reqs)):
+                i, tk = tickets.get()
+                r = server.poll(tk, -1)
+                lat[i] = time.perf_counter() - (t0 + reqs[i][0])
+                res[i] = r
+        th = threading.Thread(target=collect)
+        th.start()
+        for i, ((ta, _, _), b) in enumerate(zip(reqs, batches)):
+            d = t0 + ta - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            tickets.put((i, server.submit(b)))
+        th.join()
+    else:
+        # the plain loop: one synchronous hicops_search per request, in arrival order
+        for i, ((ta, _, _), b) in enumerate(zip(reqs, batches)):
+            d = t0 + ta - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            res[i] = idx.search(b)
+            lat[i] = time.perf_counter() - (t0 + ta)
+    end = max(t0 + r[0] + l for r, l in zip(reqs, lat))
+    return np.array(lat), end - t0, res
+
+
+def run_serving(args):
+    """Serving form: a Poisson stream of spectrum batches through the
+    continuous-batching server, against a plain one-batch-per-launch loop;
+    sustained spectra/s and p50/p99 latency per offered load, identical
+    results per request."""
+    import torch
+    from paper_2102_02286_gb300 import build as pkg_build
+    from paper_2102_02286_gb300 import hicops as hc
+
+    torch.cuda.set_device(0)
+    pkg_build.build()
+    hc.load()
+    if args.workload == "open_medium":
+        args.workload = "serving_stream"
+    w = workload(args)
+    t0 = time.perf_counter()
+    prot = synth.make_proteome(w.n_proteins, w.seed, w.protein_len)
+    pool = synth.make_spectra(prot, w)
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    idx = hc.Index(prot.seq, prot.off, w.mods, w.params)
+    t_index = time.perf_counter() - t0
+    st = idx.stats()
+    rng = np.random.default_rng(w.seed + 17)
+    # warm-up: both paths once on a small request
+    warm = pool.subset(np.arange(min(64, pool.n)))
+    idx.search(warm)
+    server = hc.Server(idx)
+    server.poll(server.submit(warm), -1)
+    sstats0 = server.stats()
+    loads = [float(x) for x in args.loads.split(",") if x]
+    rows = []
+    identical = True
+    for offered in loads:
+        reqs = poisson_requests(rng, offered, args.load_seconds, args.load_spectra, pool.n)
+        batches = request_batches(pool, reqs)
+        nspec = sum(r[2] for r in reqs)
+        lat_s, span_s, res_s = serve_stream(idx, hc, reqs, batches, server)
+        lat_p, span_p, res_p = serve_stream(idx, hc, reqs, batches, None)
+        for a, b in zip(res_s, res_p):
+            identical &= bool(np.array_equal(a.psm, b.psm) and np.array_equal(a.hist, b.hist)
+                              and np.array_equal(a.n_scored, b.n_scored))
+        row = {"offered_spectra_per_s": offered, "requests": len(reqs), "spectra": int(nspec)}
+        for name, lat, span in (("server", lat_s, span_s), ("plain_loop", lat_p, span_p)):
+            row[name] = {"spectra_per_s": nspec / span, "p50_ms": 1000 * float(np.percentile(lat, 50)),
+                         "p99_ms": 1000 * float(np.percentile(lat, 99)),
+                         "saturated": bool(nspec / span < 0.9 * offered)}
+        row["throughput_ratio"] = row["server"]["spectra_per_s"] / row["plain_loop"]["spectra_per_s"]
+        rows.append(row)
+        print(json.dumps({"load": row}), file=sys.stderr, flush=True)
+    sstats = server.stats()
+    server.close()
+    idx.close()
+    best = max(rows, key=lambda r: r["server"]["spectra_per_s"])
+    line = {
+        "metric": "sustained spectra/s and p50/p99 latency, Poisson request stream through the server",
+        "value": best["server"]["spectra_per_s"], "unit": "spectra/s",
+        "n_gpus": 1, "steps": len(loads), "warmup": 1, "ms_per_step": None,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": workload_desc(w), "n_peptides": int(st.n_peptides),
+                   "n_index_entries": int(st.n_entries), "index_bytes": int(st.device_bytes),
+                   "index_build_s": t_index, "input_gen_s": t_gen, "pool_spectra": pool.n,
+                   "batch_sizes": "log-uniform in [1, 4096]", "arrival_window_s": args.load_seconds,
+                   "server_slots": int(sstats.n_slots), "slot_bytes": int(sstats.slot_bytes),
+                   "server_launches": int(sstats.launches - sstats0.launches)},
+        "loads": rows,
+        "identical_results": identical,
+    }
+    print(json.dumps(line), flush=True)
+    return 0 if identical else 1
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "batched":
+        return run_batched(args)
+    if args.mode == "serving":
+        return run_serving(args)
     import torch
     import torch.distributed as dist
     from paper_2102_02286_gb300 import build as pkg_build
@@ -236,7 +507,13 @@ def main():
     # launch shape from the autotuner, on a sample of the batch
     t0 = time.perf_counter()
     tune_batch = hc.DeviceBatch.from_spectra(spec.subset(np.arange(min(n, args.tune_spectra))))
-    shape, tune_ms = idx.autotune(tune_batch) if args.tune_spectra > 0 else (hc.SearchConfig(), 0.0)
+    if args.shape:
+        shape, tune_ms = hc.SearchConfig(*[int(x) for x in args.shape.split(",")]), 0.0
+        idx.set_config(shape)
+    elif args.tune_spectra > 0:
+        shape, tune_ms = idx.autotune(tune_batch)
+    else:
+        shape, tune_ms = hc.SearchConfig(), 0.0
     t_tune = time.perf_counter() - t0
     del tune_batch
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
