@@ -210,6 +210,44 @@ hicops_status hicops_search_work(hicops_index* index, const hicops_batch* batch,
 
 hicops_status hicops_index_get_stats(const hicops_index* index, hicops_index_stats* out);
 
+/* ---- database sharding (paper: every process searches its own partition of
+ * the database, Superstep 3 and the Load Balancing section; the partial
+ * score distributions are added and the results assembled, Superstep 4). */
+
+/* Most shards of one database. */
+#define HICOPS_MAX_SHARDS 64u
+
+/* Shard `shard` of n_shards of a digested database (hicops_digest; need not
+ * be uploaded): the entries with pid = shard, shard + n_shards, ... (a
+ * round-robin partition of the mass-sorted order, so every shard sees every
+ * precursor window evenly).  The shard is a host-only index like
+ * hicops_digest's; hicops_index_upload builds its device part.  Its search
+ * results carry global pids, its histograms and candidate counts cover its own
+ * candidates, and its e-values are fitted to its own histogram only: combine
+ * the shards with hicops_merge_shards.  hicops_peptide on a shard takes global
+ * pids of the shard; hicops_index_copy_csr reports shard-local pids.
+ * Errors: HICOPS_EINVAL (shard >= n_shards, n_shards outside
+ * [1, HICOPS_MAX_SHARDS], index already a shard), HICOPS_ENOMEM. */
+hicops_status hicops_index_shard(const hicops_index* full, uint32_t n_shards, uint32_t shard,
+                                 hicops_index** out);
+
+/* Combines the shards' searches of the same n spectra: per spectrum, sums the
+ * histograms and candidate counts, merges the shard top-k lists by (key desc,
+ * pid asc) and fits the e-value to the summed histogram (the same merge and
+ * fit as hicops_search), so the result equals the unsharded search.
+ *   shard_psm [n_shards * n * top_k]: shard s's rows of spectrum q at
+ *   (s * n + q) * top_k; hist [hist_parts * n * 256] and nscored
+ *   [hist_parts * n]: hist_parts = n_shards (per shard, summed here) or 1
+ *   (already summed, e.g. by an all-reduce).  Outputs as hicops_search
+ *   (out_hist, out_nscored may be NULL).  on_device = 1: every buffer is a
+ *   device buffer and the work is enqueued on cuda_stream; 0: host buffers,
+ *   the call copies and waits.  Runs on the current device.
+ * Errors: HICOPS_EINVAL (sizes, NULL inputs), HICOPS_ECUDA, HICOPS_ENOMEM. */
+hicops_status hicops_merge_shards(uint32_t n_shards, uint32_t n, uint32_t top_k, const hicops_psm* shard_psm,
+                                  const uint32_t* hist, const uint32_t* nscored, uint32_t hist_parts,
+                                  int on_device, void* cuda_stream, hicops_psm* out_psm, uint32_t* out_hist,
+                                  uint32_t* out_nscored);
+
 /* Peptide pid: sequence (NUL-terminated, truncated to cap-1 letters), neutral
  * mass and the bitmask of positions carrying a variable modification (bit j =
  * residue j, 0-based).  Host only. */

@@ -77,6 +77,7 @@ def lib():
         L.or_hyperscore.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32]
         L.or_evalue.argtypes = [P, C.c_uint32, P, P, C.c_uint32, P]
         L.or_search.argtypes = [P, P, P, P, P, P, P, P, C.c_uint32, P, P, P, P, P]
+        L.or_search_shard.argtypes = [P, P, P, P, P, P, P, P, C.c_uint32, P, P, P, P, P, C.c_uint32, C.c_uint32]
     return _lib
 
 
@@ -151,7 +152,9 @@ class OracleDb:
         n = lib().or_db_bins(self.h, pid, _ptr(b), _ptr(t))
         return b[:n].copy(), t[:n].copy()
 
-    def search(self, spec, sel=None) -> SearchResult:
+    def search(self, spec, sel=None, n_shards: int = 1, shard: int = 0) -> SearchResult:
+        """Search the selected spectra; with n_shards > 1 only the database
+        entries pid = shard (mod n_shards) are candidates."""
         n = spec.n
         sel = np.arange(n, dtype=np.uint32) if sel is None else np.ascontiguousarray(sel, dtype=np.uint32)
         k, H = self.top_k, self.hist_bins
@@ -163,8 +166,8 @@ class OracleDb:
         a = [np.ascontiguousarray(x) for x in (spec.peak_off.astype(np.uint64), spec.mz.astype(np.float32),
                                                spec.intensity.astype(np.float32), spec.prec_mz.astype(np.float64),
                                                spec.charge.astype(np.uint8), spec.tol_da.astype(np.float64))]
-        lib().or_search(self.h, *[_ptr(x) for x in a], _ptr(sel), len(sel), _ptr(psm), _ptr(hist),
-                        _ptr(ns), _ptr(lo), _ptr(hi))
+        lib().or_search_shard(self.h, *[_ptr(x) for x in a], _ptr(sel), len(sel), _ptr(psm), _ptr(hist),
+                              _ptr(ns), _ptr(lo), _ptr(hi), n_shards, shard)
         return SearchResult(psm, hist, ns, lo, hi)
 
 

@@ -413,11 +413,13 @@ void or_evalue(const uint32_t* hist, uint32_t nbins, const int64_t* keys, const 
 // Search the selected spectra (indices sel[0..n_sel-1] of the batch).
 // Outputs per selected spectrum: psm[top_k], hist[hist_bins], n_scored,
 // window [lo, hi).
-void or_search(void* h, const uint64_t* peak_off, const float* mz, const float* inten,
-               const double* prec_mz, const uint8_t* charge, const double* tol,
-               const uint32_t* sel, uint32_t n_sel,
-               OrPsm* out_psm, uint32_t* out_hist, uint32_t* out_nscored,
-               uint32_t* out_lo, uint32_t* out_hi) {
+// With n_shards > 1 only the database entries pid = shard (mod n_shards)
+// are candidates: the partition one process searches (Superstep 3).
+void or_search_shard(void* h, const uint64_t* peak_off, const float* mz, const float* inten,
+                     const double* prec_mz, const uint8_t* charge, const double* tol,
+                     const uint32_t* sel, uint32_t n_sel,
+                     OrPsm* out_psm, uint32_t* out_hist, uint32_t* out_nscored,
+                     uint32_t* out_lo, uint32_t* out_hi, uint32_t n_shards, uint32_t shard) {
     const Db* db = (Db*)h;
     const OrParams& p = db->p;
     const uint32_t K = p.top_k, H = p.hist_bins;
@@ -436,6 +438,7 @@ void or_search(void* h, const uint64_t* peak_off, const float* mz, const float* 
             lo = (uint32_t)(std::lower_bound(masses.begin(), masses.end(), q.Mq - q.tol) - masses.begin());
             hi = (uint32_t)(std::upper_bound(masses.begin(), masses.end(), q.Mq + q.tol) - masses.begin());
             for (uint32_t pid = lo; pid < hi; ++pid) {
+                if (pid % n_shards != shard) continue;
                 // filter_2: shared peaks between query bins and the peptide's ion bins
                 auto ib = ion_bins(*db, db->peps[pid]);
                 uint32_t nb = 0, ny = 0, S = 0;
@@ -473,6 +476,15 @@ void or_search(void* h, const uint64_t* peak_off, const float* mz, const float* 
         if (out_lo) out_lo[si] = lo;
         if (out_hi) out_hi[si] = hi;
     }
+}
+
+void or_search(void* h, const uint64_t* peak_off, const float* mz, const float* inten,
+               const double* prec_mz, const uint8_t* charge, const double* tol,
+               const uint32_t* sel, uint32_t n_sel,
+               OrPsm* out_psm, uint32_t* out_hist, uint32_t* out_nscored,
+               uint32_t* out_lo, uint32_t* out_hi) {
+    or_search_shard(h, peak_off, mz, inten, prec_mz, charge, tol, sel, n_sel, out_psm, out_hist, out_nscored,
+                    out_lo, out_hi, 1, 0);
 }
 
 }  // extern "C"

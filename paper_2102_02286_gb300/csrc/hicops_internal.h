@@ -89,6 +89,10 @@ struct hicops_index {
     std::vector<uint32_t> base;
     std::vector<uint64_t> mask;
 
+    // a shard of a database holds its entries pid_base, pid_base + pid_stride, ...:
+    // global pid = local pid * pid_stride + pid_base (1 and 0 for a whole database)
+    uint32_t pid_stride = 1, pid_base = 0;
+
     uint32_t n_bins = 0;           // bins 0 .. n_bins-1 (absolute bin numbers)
     uint64_t s_max = 0;            // largest possible S
     hicops_index_stats stats{};

@@ -349,10 +349,59 @@ extern "C" hicops_status hicops_index_get_stats(const hicops_index* idx, hicops_
     return HICOPS_OK;
 }
 
+extern "C" hicops_status hicops_index_shard(const hicops_index* full, uint32_t n_shards, uint32_t shard,
+                                            hicops_index** out) {
+    if (!full || !out) { set_error("NULL argument"); return HICOPS_EINVAL; }
+    *out = nullptr;
+    if (full->pid_stride != 1) { set_error("the index is already a shard"); return HICOPS_EINVAL; }
+    if (n_shards < 1 || n_shards > HICOPS_MAX_SHARDS || shard >= n_shards) {
+        set_error("shard %u of %u: need 1 <= n_shards <= %u and shard < n_shards", shard, n_shards,
+                  (unsigned)HICOPS_MAX_SHARDS);
+        return HICOPS_EINVAL;
+    }
+    hicops_index* idx = new (std::nothrow) hicops_index();
+    if (!idx) { set_error("out of host memory"); return HICOPS_ENOMEM; }
+    idx->p = full->p;
+    memcpy(idx->mres, full->mres, sizeof(idx->mres));
+    memcpy(idx->mmod, full->mmod, sizeof(idx->mmod));
+    memcpy(idx->var_type, full->var_type, sizeof(idx->var_type));
+    idx->n_var = full->n_var;
+    idx->var_delta = full->var_delta;
+    idx->var_max = full->var_max;
+    idx->residues = full->residues;
+    idx->base_off = full->base_off;
+    const size_t P = full->mass.size();
+    const size_t n = P > shard ? (P - shard + n_shards - 1) / n_shards : 0;
+    idx->mass.resize(n);
+    idx->base.resize(n);
+    idx->mask.resize(n);
+    for (size_t i = 0; i < n; ++i) {   // round-robin over the mass-sorted order
+        const size_t g = i * n_shards + shard;
+        idx->mass[i] = full->mass[g];
+        idx->base[i] = full->base[g];
+        idx->mask[i] = full->mask[g];
+    }
+    idx->pid_stride = n_shards;
+    idx->pid_base = shard;
+    idx->n_bins = full->n_bins;
+    idx->s_max = full->s_max;
+    idx->stats = hicops_index_stats{};
+    idx->stats.n_peptides = n;
+    idx->stats.n_base_peptides = full->stats.n_base_peptides;
+    idx->stats.n_bins = full->n_bins;
+    *out = idx;
+    return HICOPS_OK;
+}
+
 extern "C" hicops_status hicops_peptide(const hicops_index* idx, uint32_t pid, char* seq, uint32_t cap,
                                         double* mass, uint64_t* modmask) {
     if (!idx) { set_error("index is NULL"); return HICOPS_EINVAL; }
-    if (pid >= idx->mass.size()) { set_error("pid %u out of range", pid); return HICOPS_EINVAL; }
+    if (pid < idx->pid_base || (pid - idx->pid_base) % idx->pid_stride != 0) {
+        set_error("pid %u is not in this shard", pid);
+        return HICOPS_EINVAL;
+    }
+    pid = (pid - idx->pid_base) / idx->pid_stride;
+    if (pid >= idx->mass.size()) { set_error("pid out of range"); return HICOPS_EINVAL; }
     const uint32_t b = idx->base[pid];
     const uint64_t a = idx->base_off[b], e = idx->base_off[b + 1];
     if (seq && cap) {

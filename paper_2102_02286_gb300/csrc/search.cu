@@ -205,7 +205,7 @@ hicops_status enqueue_search(hicops_index* idx, const DevBatch& d, uint32_t n, c
     hicops_status st = launch_search(sa, cfg, (uint64_t)n * max_seg, s);
     if (st != HICOPS_OK) return st;
     mark(idx, 3, s, timing_marks);
-    MergeArgs ma{w.seg_off, w.utop, d_hist, n, k, 0, d_psm};
+    MergeArgs ma{w.seg_off, w.utop, d_hist, n, k, 0, d_psm, idx->pid_stride, idx->pid_base};
     merge_kernel<<<n, kMergeThreads, 0, s>>>(ma);
     count_launches(1);
     HC_CUDA(cudaGetLastError());
@@ -629,4 +629,107 @@ extern "C" hicops_status hicops_search_noalloc(hicops_index* idx, const hicops_b
     const DevBatch d{b->peak_off, b->mz, b->intensity, b->prec_mz, b->charge, b->prec_tol_da};
     return enqueue_search(idx, d, n, w, idx->dev.cfg, out_psm, out_hist ? out_hist : w.hist,
                           out_nscored ? out_nscored : w.ns, (cudaStream_t)b->cuda_stream, false);
+}
+
+// ---- database sharding (paper: each process searches its partition of the
+// database, Superstep 3; the partial score distributions are added and the
+// results assembled, Superstep 4).  A shard's rows carry global pids; the
+// merge sums the partial histograms and candidate counts, merges the shard
+// top-k lists by (key desc, pid asc) with merge_kernel and fits the e-value
+// to the summed histogram, so the result equals the unsharded search.
+namespace hicops {
+namespace {
+
+// one block per spectrum: shard rows -> unit lists, summed histogram
+__global__ void shard_gather_kernel(const hicops_psm* __restrict__ parts, uint32_t n_shards, uint32_t n,
+                                    uint32_t k, const uint32_t* __restrict__ hist_in,
+                                    const uint32_t* __restrict__ ns_in, uint32_t hist_parts,
+                                    UnitTop* __restrict__ utop, uint64_t* __restrict__ seg_off,
+                                    uint32_t* __restrict__ hist, uint32_t* __restrict__ ns) {
+    const uint32_t q = blockIdx.x;
+    for (uint32_t i = threadIdx.x; i < n_shards * k; i += blockDim.x) {
+        const uint32_t s = i / k, r = i % k;
+        const hicops_psm row = parts[((uint64_t)s * n + q) * k + r];
+        UnitTop t;
+        t.key = row.key;
+        t.pid = row.pid;
+        t.packed = ((uint32_t)row.nb << kNbShift) | ((uint32_t)row.ny << kNyShift);
+        utop[((uint64_t)q * n_shards + s) * k + r] = t;
+    }
+    for (uint32_t j = threadIdx.x; j < kHistBins; j += blockDim.x) {
+        uint32_t h = 0;
+        for (uint32_t p = 0; p < hist_parts; ++p) h += hist_in[((uint64_t)p * n + q) * kHistBins + j];
+        hist[(uint64_t)q * kHistBins + j] = h;
+    }
+    if (threadIdx.x == 0) {
+        uint32_t c = 0;
+        for (uint32_t p = 0; p < hist_parts; ++p) c += ns_in[(uint64_t)p * n + q];
+        ns[q] = c;
+        seg_off[q] = (uint64_t)q * n_shards;
+        if (q == n - 1) seg_off[n] = (uint64_t)n * n_shards;
+    }
+}
+
+}  // namespace
+}  // namespace hicops
+
+extern "C" hicops_status hicops_merge_shards(uint32_t n_shards, uint32_t n, uint32_t top_k,
+                                             const hicops_psm* shard_psm, const uint32_t* hist,
+                                             const uint32_t* nscored, uint32_t hist_parts, int on_device,
+                                             void* cuda_stream, hicops_psm* out_psm, uint32_t* out_hist,
+                                             uint32_t* out_nscored) {
+    if (n_shards < 1 || n_shards > HICOPS_MAX_SHARDS) {
+        set_error("n_shards must be in [1, %u]", (unsigned)HICOPS_MAX_SHARDS);
+        return HICOPS_EINVAL;
+    }
+    if (top_k < 1 || top_k > kMaxTopK) { set_error("top_k must be in [1, %u]", kMaxTopK); return HICOPS_EINVAL; }
+    if (hist_parts != 1 && hist_parts != n_shards) { set_error("hist_parts must be 1 or n_shards"); return HICOPS_EINVAL; }
+    if (n == 0) return HICOPS_OK;
+    if (!shard_psm || !hist || !nscored || !out_psm) { set_error("NULL argument"); return HICOPS_EINVAL; }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    {
+        Scratch sc(s);
+        const hicops_psm* d_parts = shard_psm;
+        const uint32_t *d_hin = hist, *d_nin = nscored;
+        const uint64_t rows = (uint64_t)n_shards * n * top_k;
+        if (!on_device) {
+            hicops_psm* p;
+            uint32_t *h, *c;
+            HC_CUDA(sc.get(&p, rows));
+            HC_CUDA(sc.get(&h, (uint64_t)hist_parts * n * kHistBins));
+            HC_CUDA(sc.get(&c, (uint64_t)hist_parts * n));
+            HC_CUDA(cudaMemcpyAsync(p, shard_psm, sizeof(hicops_psm) * rows, cudaMemcpyHostToDevice, s));
+            HC_CUDA(cudaMemcpyAsync(h, hist, sizeof(uint32_t) * hist_parts * n * kHistBins, cudaMemcpyHostToDevice, s));
+            HC_CUDA(cudaMemcpyAsync(c, nscored, sizeof(uint32_t) * hist_parts * n, cudaMemcpyHostToDevice, s));
+            d_parts = p;
+            d_hin = h;
+            d_nin = c;
+        }
+        UnitTop* utop;
+        uint64_t* seg_off;
+        uint32_t *d_hist, *d_ns;
+        hicops_psm* d_out = on_device ? out_psm : nullptr;
+        HC_CUDA(sc.get(&utop, rows));
+        HC_CUDA(sc.get(&seg_off, (uint64_t)n + 1));
+        if (on_device && out_hist) d_hist = out_hist; else HC_CUDA(sc.get(&d_hist, (uint64_t)n * kHistBins));
+        if (on_device && out_nscored) d_ns = out_nscored; else HC_CUDA(sc.get(&d_ns, n));
+        if (!d_out) HC_CUDA(sc.get(&d_out, (uint64_t)n * top_k));
+        shard_gather_kernel<<<n, 256, 0, s>>>(d_parts, n_shards, n, top_k, d_hin, d_nin, hist_parts, utop,
+                                              seg_off, d_hist, d_ns);
+        count_launches(1);
+        HC_CUDA(cudaGetLastError());
+        MergeArgs ma{seg_off, utop, d_hist, n, top_k, 0, d_out, 1u, 0u};
+        merge_kernel<<<n, kMergeThreads, 0, s>>>(ma);
+        count_launches(1);
+        HC_CUDA(cudaGetLastError());
+        if (!on_device) {
+            HC_CUDA(cudaMemcpyAsync(out_psm, d_out, sizeof(hicops_psm) * n * top_k, cudaMemcpyDeviceToHost, s));
+            if (out_hist)
+                HC_CUDA(cudaMemcpyAsync(out_hist, d_hist, sizeof(uint32_t) * n * kHistBins, cudaMemcpyDeviceToHost, s));
+            if (out_nscored)
+                HC_CUDA(cudaMemcpyAsync(out_nscored, d_ns, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, s));
+        }
+    }
+    if (!on_device) HC_CUDA(cudaStreamSynchronize(s));
+    return HICOPS_OK;
 }

@@ -184,6 +184,7 @@ struct MergeArgs {
     uint32_t n, k;
     uint32_t q_base;          // query index written into the rows
     hicops_psm* out;
+    uint32_t pid_stride, pid_base;   // row pid = list pid * pid_stride + pid_base
 };
 
 __device__ __forceinline__ double block_sum(double v, double* red) {
@@ -300,7 +301,7 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(MergeArgs a) {
         const bool real = (int)r < m && sk[r] != kNoIdx && buf[sk[r]].pid != 0xffffffffu;
         if (real) {
             const UnitTop t = buf[sk[r]];
-            o.pid = t.pid;
+            o.pid = t.pid * a.pid_stride + a.pid_base;
             o.nb = (uint8_t)(t.packed >> kNbShift);
             o.ny = (uint8_t)((t.packed >> kNyShift) & 63u);
             o.key = t.key;

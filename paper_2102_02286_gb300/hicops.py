@@ -133,6 +133,8 @@ def load(build_if_missing: bool = False):
         "hicops_index_last_timing": (st, [P, C.POINTER(Timing)]),
         "hicops_kernel_launches": (C.c_uint64, []),
         "hicops_index_get_stats": (st, [P, C.POINTER(IndexStats)]),
+        "hicops_index_shard": (st, [P, C.c_uint32, C.c_uint32, C.POINTER(P)]),
+        "hicops_merge_shards": (st, [C.c_uint32, C.c_uint32, C.c_uint32, P, P, P, C.c_uint32, C.c_int, P, P, P, P]),
         "hicops_peptide": (st, [P, C.c_uint32, C.c_char_p, C.c_uint32, P, P]),
         "hicops_index_copy_csr": (st, [P, P, P]),
         "hicops_index_free": (None, [P]),
@@ -193,6 +195,24 @@ class Index:
         self._keep = None
         if upload:
             self.upload()
+
+    @classmethod
+    def _from_handle(cls, h, params):
+        self = cls.__new__(cls)
+        self.params = params
+        self.top_k = params.top_k
+        self.h = h
+        self._keep = None
+        return self
+
+    def shard(self, n_shards: int, shard: int, upload: bool = True) -> "Index":
+        """hicops_index_shard: entries pid = shard (mod n_shards); results carry global pids."""
+        h = C.c_void_p()
+        _check(load().hicops_index_shard(self.h, n_shards, shard, C.byref(h)))
+        s = Index._from_handle(h, self.params)
+        if upload:
+            s.upload()
+        return s
 
     def upload(self):
         _check(load().hicops_index_upload(self.h))
@@ -426,3 +446,30 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def merge_shards(n_shards: int, n: int, top_k: int, psm, hist, n_scored, hist_parts: int,
+                 stream=None) -> "DeviceResult":
+    """hicops_merge_shards on device tensors (asynchronous on the stream):
+    psm [n_shards * n * top_k] rows, hist [hist_parts * n * 256], n_scored
+    [hist_parts * n]; returns a DeviceResult of the merged search."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    out = DeviceResult.alloc(n, top_k)
+    _check(load().hicops_merge_shards(n_shards, n, top_k, psm.data_ptr(), hist.data_ptr(), n_scored.data_ptr(),
+                                      hist_parts, 1, s.cuda_stream, out.psm.data_ptr(), out.hist.data_ptr(),
+                                      out.n_scored.data_ptr()))
+    return out
+
+
+def merge_shards_host(n_shards: int, n: int, top_k: int, psm: np.ndarray, hist: np.ndarray,
+                      n_scored: np.ndarray, hist_parts: int) -> SearchResult:
+    """hicops_merge_shards on host arrays (the library copies to the device and back)."""
+    psm = np.ascontiguousarray(psm, PSM_DTYPE)
+    hist = np.ascontiguousarray(hist, np.uint32)
+    n_scored = np.ascontiguousarray(n_scored, np.uint32)
+    out = SearchResult(np.zeros((n, top_k), PSM_DTYPE), np.zeros((n, HIST_BINS), np.uint32),
+                       np.zeros(n, np.uint32))
+    _check(load().hicops_merge_shards(n_shards, n, top_k, _ptr(psm), _ptr(hist), _ptr(n_scored), hist_parts, 0,
+                                      None, _ptr(out.psm), _ptr(out.hist), _ptr(out.n_scored)))
+    return out
