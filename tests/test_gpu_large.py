@@ -1,0 +1,73 @@
+"""The large modified open search (50k proteins, Met-ox <= 3, STY-phospho <= 2,
+N/Q-deamidation <= 1, dF 0.02 Da, top-10) at full index size, and the
+serving recipe's spectra on the same index, sampled against the oracle.
+
+The oracle digests the whole database on one core before it can find a
+window (minutes), and a +-500 Da window of this database takes it minutes
+per spectrum, so the sampled spectra are searched by oracle processes in
+parallel (spawned, so no process forks after the GPU is in use), and the
+module runs only with HICOPS_LARGE=1."""
+import concurrent.futures as cf
+import multiprocessing as mp
+import os
+
+import numpy as np
+import pytest
+
+from paper_2102_02286_gb300 import configs, synth
+from paper_2102_02286_gb300 import hicops as hc
+
+from parity import PAD, assert_parity
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow,
+              pytest.mark.skipif(os.environ.get("HICOPS_LARGE") != "1", reason="set HICOPS_LARGE=1")]
+
+
+def _oracle_one(workload_name, n_spectra, q):
+    """(in a spawned process) the oracle's result for spectrum q of the
+    workload's first n_spectra spectra on the open_large database."""
+    import oracle
+    oracle.build()
+    w = configs.BY_NAME[workload_name].with_spectra(n_spectra)
+    prot = synth.make_proteome(w.n_proteins, w.seed, w.protein_len)
+    spec = synth.make_spectra(prot, w)
+    db = oracle.OracleDb(prot.seq, prot.off, w.mods, w.params)
+    return db.search(spec, sel=np.array([q], dtype=np.uint32))
+
+
+def test_open_large_and_serving_recipe_sampled(oracle_lib):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    torch.cuda.set_device(0)
+    from paper_2102_02286_gb300 import build as pkg_build
+    pkg_build.build()
+    wl = configs.OPEN_LARGE.with_spectra(20000)
+    ws = configs.SERVING_STREAM.with_spectra(4096)
+    prot = synth.make_proteome(wl.n_proteins, wl.seed, wl.protein_len)
+    spec_l = synth.make_spectra(prot, wl)
+    spec_s = synth.make_spectra(prot, ws)
+    npk = np.diff(spec_s.peak_off.astype(np.int64))
+    s_sel = [int(np.flatnonzero(spec_s.tol_da == t)[np.argmax(npk[spec_s.tol_da == t])]) for t in (10.0, 500.0)]
+    l_sel = [0, 19999]
+    jobs = [("open_large", wl.spectra.n_spectra, q) for q in l_sel] + \
+           [("serving_stream", ws.spectra.n_spectra, q) for q in s_sel]
+    with cf.ProcessPoolExecutor(len(jobs), mp_context=mp.get_context("spawn")) as ex:
+        futs = [ex.submit(_oracle_one, *j) for j in jobs]
+        idx = hc.Index(prot.seq, prot.off, wl.mods, wl.params)
+        st = idx.stats()
+        got_l = idx.search(spec_l)                       # one batch of 20k spectra
+        server = hc.Server(idx)
+        got_s = server.poll(server.submit(spec_s), -1)   # the serving path
+        server.close()
+        refs = [f.result() for f in futs]
+    assert st.n_peptides > 100_000_000
+    for i, q in enumerate(l_sel):
+        sel = np.array([q], dtype=np.uint32)
+        assert_parity(got_l, refs[i], sel=sel, label=f"open_large spectrum {q}")
+    for i, q in enumerate(s_sel):
+        sel = np.array([q], dtype=np.uint32)
+        assert_parity(got_s, refs[len(l_sel) + i], sel=sel, label=f"serving recipe spectrum {q}")
+    real = got_l.psm["pid"] != PAD
+    np.testing.assert_array_equal(got_l.hist.sum(1), got_l.n_scored)
+    assert np.all(got_l.psm["nb"][real].astype(int) + got_l.psm["ny"][real] >= wl.params.min_shared)

@@ -223,3 +223,35 @@ def test_parity_open_medium_full_index_sampled(gpu, oracle_lib):
                   | ~real[:, 1:])
     np.testing.assert_array_equal(got.hist.sum(1), got.n_scored)
     assert np.all(got.psm["nb"][real].astype(int) + got.psm["ny"][real] >= w.params.min_shared)
+
+
+@pytest.mark.slow
+def test_parity_uneven_batched_full_sampled(gpu, oracle_lib):
+    """The uneven 200k-spectrum batch (50-500 peaks, +-10/100/500 Da) on the
+    open-search index in the batched form the benchmark times: one plan
+    launch with the autotuned shape, replayed as a CUDA graph; spectra of
+    every tolerance class and both peak-count extremes checked against the
+    oracle."""
+    torch = gpu
+    w = configs.UNEVEN_BATCHED
+    prot, idx, db = build_both(oracle_lib, w)
+    spec = synth.make_spectra(prot, w)
+    dbat = hc.DeviceBatch.from_spectra(spec)
+    shape, _ = idx.autotune(hc.DeviceBatch.from_spectra(spec.subset(np.arange(20000))))
+    plan = idx.plan(spec.n, shape)
+    out = hc.DeviceResult.alloc(spec.n, w.params.top_k)
+    stream = torch.cuda.Stream()
+    for _ in range(2):                       # capture, then replay
+        with torch.cuda.stream(stream):
+            plan.search(dbat, out, stream, graph=True)
+    stream.synchronize()
+    got = out.to_host(spec.n, w.params.top_k)
+    plan.close()
+    npk = np.diff(spec.peak_off.astype(np.int64))
+    sel = []
+    for tol in (10.0, 100.0, 500.0):
+        cls = np.flatnonzero(spec.tol_da == tol)
+        sel += [int(cls[np.argmin(npk[cls])]), int(cls[np.argmax(npk[cls])])]
+    sel = np.array(sorted(sel), dtype=np.uint32)
+    assert_parity(got, db.search(spec, sel=sel), sel=sel, label="uneven_batched")
+    np.testing.assert_array_equal(got.hist.sum(1), got.n_scored)
