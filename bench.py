@@ -176,7 +176,7 @@ def run_reference(args):
         return 0
     import oracle
     w = workload(args)
-    prot = synth.make_proteome(w.n_proteins, w.seed, w.protein_len)
+    prot = synth.make_proteome(w.n_proteins, w.db_seed, w.protein_len)
     spec = synth.make_spectra(prot, w)
     db = oracle.OracleDb(prot.seq, prot.off, w.mods, w.params)
     per_step = max(1, args.oracle_spectra // 3)
@@ -230,7 +230,7 @@ def run_batched(args):
     if args.workload == "open_medium":
         args.workload = "uneven_batched"
     w = workload(args)
-    prot = synth.make_proteome(w.n_proteins, w.seed, w.protein_len)
+    prot = synth.make_proteome(w.n_proteins, w.db_seed, w.protein_len)
     spec = synth.make_spectra(prot, w)
     idx = hc.Index(prot.seq, prot.off, w.mods, w.params)
     n, k = spec.n, w.params.top_k
@@ -397,7 +397,7 @@ def run_serving(args):
         args.workload = "serving_stream"
     w = workload(args)
     t0 = time.perf_counter()
-    prot = synth.make_proteome(w.n_proteins, w.seed, w.protein_len)
+    prot = synth.make_proteome(w.n_proteins, w.db_seed, w.protein_len)
     pool = synth.make_spectra(prot, w)
     t_gen = time.perf_counter() - t0
     t0 = time.perf_counter()
@@ -479,7 +479,7 @@ def main():
     hc.load()
     w = workload(args)
     t0 = time.perf_counter()
-    prot = synth.make_proteome(w.n_proteins, w.seed, w.protein_len)
+    prot = synth.make_proteome(w.n_proteins, w.db_seed, w.protein_len)
     spec = synth.make_spectra(prot, w, seed=w.seed + 7919 * rank)
     t_gen = time.perf_counter() - t0
     t0 = time.perf_counter()

@@ -79,10 +79,17 @@ class Workload:
     spectra: SpectraRecipe
     protein_len: Tuple[int, int] = (100, 800)
     description: str = ""
+    db_index: int = -1               # workload whose database this one searches (-1: its own)
 
     @property
     def seed(self) -> int:
+        """Seed of the workload's spectra."""
         return BASE_SEED + self.index
+
+    @property
+    def db_seed(self) -> int:
+        """Seed of the proteome (shared with the workload named by db_index)."""
+        return BASE_SEED + (self.db_index if self.db_index >= 0 else self.index)
 
     def with_spectra(self, n: int) -> "Workload":
         return replace(self, spectra=replace(self.spectra, n_spectra=n))
@@ -116,7 +123,7 @@ OPEN_LARGE = Workload(
 )
 
 UNEVEN_BATCHED = Workload(
-    name="uneven_batched", index=3, n_proteins=20_000,
+    name="uneven_batched", index=3, n_proteins=20_000, db_index=1,
     mods=(CARBAMIDOMETHYL_C, OX_M(2), PHOSPHO_STY(1)),
     params=SearchParams(missed_cleavages=2, bin_width_da=0.01, top_n_peaks=500, min_shared=4, top_k=5),
     spectra=SpectraRecipe(n_spectra=200_000, target_peaks=(50, 500), charges=(2, 3), tol_da=(10.0, 100.0, 500.0)),
@@ -124,7 +131,7 @@ UNEVEN_BATCHED = Workload(
 )
 
 SERVING_STREAM = Workload(
-    name="serving_stream", index=4, n_proteins=50_000,
+    name="serving_stream", index=4, n_proteins=50_000, db_index=2,
     mods=(CARBAMIDOMETHYL_C, OX_M(3), PHOSPHO_STY(2), DEAMID_NQ(1)),
     params=SearchParams(missed_cleavages=2, bin_width_da=0.02, top_n_peaks=500, min_shared=4, top_k=10),
     spectra=SpectraRecipe(n_spectra=100_000, target_peaks=(50, 500), charges=(2, 3, 4), tol_da=(10.0, 500.0)),

@@ -448,7 +448,7 @@ extern "C" hicops_status hicops_autotune(hicops_index* idx, const hicops_batch* 
     if (st != HICOPS_OK) return st;
     if (!b->on_device || b->n == 0) { set_error("autotune needs a non-empty device batch"); return HICOPS_EINVAL; }
     const uint32_t cand_threads[2] = {256, 512};
-    const uint32_t cand_cm[2] = {2, 4};   // chunk_entries
+    const uint32_t cand_cm[4] = {2, 3, 4, 5};   // chunk_entries
     const uint32_t cand_ctas[2] = {0, 1};
     const uint32_t cand_seg[3] = {0, 1u << 18, 1u << 16};
     cudaStream_t s = (cudaStream_t)b->cuda_stream;

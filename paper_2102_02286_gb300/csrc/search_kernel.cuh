@@ -14,7 +14,7 @@
 //           prefix sum; lane l of a warp takes entries l, l + 32, ...) sets
 //           the peptide's bit in a "seen" bit-plane and, when it was set, in
 //           a "twice" plane (shared-memory atomicOr), and is logged in shared
-//           memory as (peptide offset | isY << 17 | peak << 18); first bits
+//           memory as (peptide offset << 1 | isY | peak << 18); first bits
 //           set in the twice plane are counted;
 //   mark    only when nslices >= min_shared - 1 (peptides seen once with
 //           enough hot bits are candidates too) or when there are more than
@@ -498,20 +498,59 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel
 
         // ---- a super-chunk in passes (see the header); entries of parity
         // buffer buf, peptide ids [x0, x1) of the span starting at cb
+        // Pass A over the entries of parity buffer buf (the walk of
+        // for_each_entry, specialised): per batch of kJ entries a lane first
+        // issues all its loads, then all its seen-plane atomics, then the
+        // twice-plane atomics of the second hits, so the latencies overlap.
+        // A log record is (entry - 2 cb) | peak << 18, i.e. offset << 1 |
+        // isY in bits 0..17.
         auto pass_a = [&](int buf, uint32_t cb, uint32_t x0, uint32_t x1, int par) {
+            constexpr int kJ = 8;
+            const uint32_t R = sh.pre[buf][nnorm];
+            const uint32_t per = warp_share<THREADS>(R);
+            const uint32_t f0 = (uint32_t)warp * per, f1 = min(R, f0 + per);
             uint32_t fresh = 0;   // twice bits this lane set first
-            for_each_entry(buf, [&](uint32_t f, uint32_t e, int li) {
-                const uint32_t pid = e >> 1;
-                uint32_t rec = 0xffffffffu;
-                if (pid >= x0 && pid < x1) {
-                    const uint32_t off = pid - cb;
-                    const uint32_t bit = 1u << (off & 31);
-                    if (atomicOr(&seen[off >> 5], bit) & bit)
-                        fresh += (atomicOr(&twice[off >> 5], bit) & bit) ? 0u : 1u;
-                    rec = off | ((e & 1u) << 17) | ((uint32_t)li << 18);
+            if (f0 < f1) {
+                int li = sh.wli[buf][warp];
+                uint32_t nxt = sh.pre[buf][li + 1];
+                const uint32_t* gp = a.entry + (sh.pbase[li] + sh.rs[buf][li] - sh.pre[buf][li]);
+                uint32_t lsh = (uint32_t)li << 18;
+                const uint32_t e_lo = x0 << 1, e_hi = x1 << 1, e_cb = cb << 1;   // entries of pids in [x0, x1)
+                for (uint32_t fb = f0 + lane; fb < f1; fb += 32 * kJ) {
+                    uint32_t ev[kJ], lr[kJ];
+#pragma unroll
+                    for (int j = 0; j < kJ; ++j) {
+                        const uint32_t f = fb + 32 * j;
+                        ev[j] = 0xffffffffu;   // above e_hi: out of range
+                        lr[j] = 0u;
+                        if (f < f1) {
+                            while (f >= nxt) {
+                                ++li;
+                                nxt = sh.pre[buf][li + 1];
+                                gp = a.entry + (sh.pbase[li] + sh.rs[buf][li] - sh.pre[buf][li]);
+                                lsh = (uint32_t)li << 18;
+                            }
+                            lr[j] = lsh;
+                            ev[j] = __ldg(gp + f);
+                        }
+                    }
+                    uint32_t old[kJ], bitv[kJ], wd[kJ];
+#pragma unroll
+                    for (int j = 0; j < kJ; ++j) {
+                        const bool in = ev[j] >= e_lo && ev[j] < e_hi;
+                        const uint32_t o2 = ev[j] - e_cb;
+                        const uint32_t off = o2 >> 1;
+                        bitv[j] = in ? 1u << (off & 31) : 0u;
+                        wd[j] = off >> 5;
+                        old[j] = in ? atomicOr(&seen[wd[j]], bitv[j]) : 0u;
+                        const uint32_t f = fb + 32 * j;
+                        if (f < f1) logw[f] = in ? (o2 | lr[j]) : 0xffffffffu;
+                    }
+#pragma unroll
+                    for (int j = 0; j < kJ; ++j)
+                        if (old[j] & bitv[j]) fresh += (atomicOr(&twice[wd[j]], bitv[j]) & bitv[j]) ? 0u : 1u;
                 }
-                logw[f] = rec;
-            });
+            }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) fresh += __shfl_xor_sync(0xffffffffu, fresh, o);
             if (lane == 0 && fresh) atomicAdd(&sh.ncand[par], fresh);
@@ -583,21 +622,34 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel
             if (tid == 0) sh.nrounds = (int)(total ? (total - 1) / kRound + 1 : 0);
             __syncthreads();
         };
+        // Replay of the log: 4 records per thread in flight, then their
+        // twice-plane words, then the inserts of the candidates' entries.
         auto replay = [&](uint32_t R, uint32_t wlo, uint32_t whi) {
-            for (uint32_t i = tid; i < R; i += THREADS) {
-                const uint32_t rec = logw[i];
-                if (rec == 0xffffffffu) continue;
-                const uint32_t off = rec & 0x1ffffu;
-                const uint32_t w = off >> 5;
-                if (!((twice[w] >> (off & 31)) & 1u) || w < wlo || w >= whi) continue;
-                const uint32_t v = counter_inc_y((rec >> 17) & 1u, sh.pinc[rec >> 18]);
-                const unsigned long long item = ((unsigned long long)off << 32) | v;
-                uint32_t sl = slot_of(off);
-                for (uint32_t probe = 0; probe < kSlots; ++probe) {
-                    const unsigned long long old = atomicCAS(&tab[sl], 0ull, item);
-                    if (old == 0ull) break;
-                    if ((uint32_t)(old >> 32) == off) { atomicAdd(&tab[sl], (unsigned long long)v); break; }
-                    sl = (sl + 1) & (kSlots - 1);
+            constexpr int kU = 4;
+            for (uint32_t i0 = tid; i0 < R; i0 += kU * THREADS) {
+                uint32_t rec[kU], tw[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const uint32_t i = i0 + u * THREADS;
+                    rec[u] = i < R ? logw[i] : 0xffffffffu;
+                }
+#pragma unroll
+                for (int u = 0; u < kU; ++u)
+                    tw[u] = rec[u] != 0xffffffffu ? twice[(rec[u] & 0x3ffffu) >> 6] : 0u;
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const uint32_t off = (rec[u] & 0x3ffffu) >> 1;
+                    const uint32_t w = off >> 5;
+                    if (rec[u] == 0xffffffffu || !((tw[u] >> (off & 31)) & 1u) || w < wlo || w >= whi) continue;
+                    const uint32_t v = counter_inc_y(rec[u] & 1u, sh.pinc[rec[u] >> 18]);
+                    const unsigned long long item = ((unsigned long long)off << 32) | v;
+                    uint32_t sl = slot_of(off);
+                    for (uint32_t probe = 0; probe < kSlots; ++probe) {
+                        const unsigned long long old = atomicCAS(&tab[sl], 0ull, item);
+                        if (old == 0ull) break;
+                        if ((uint32_t)(old >> 32) == off) { atomicAdd(&tab[sl], (unsigned long long)v); break; }
+                        sl = (sl + 1) & (kSlots - 1);
+                    }
                 }
             }
         };

@@ -213,7 +213,7 @@ def make_spectra(prot: Proteome, w: Workload, n: Optional[int] = None, seed: Opt
 
 
 def make_workload_inputs(w: Workload, n_spectra: Optional[int] = None):
-    prot = make_proteome(w.n_proteins, w.seed, w.protein_len)
+    prot = make_proteome(w.n_proteins, w.db_seed, w.protein_len)
     spec = make_spectra(prot, w, n_spectra)
     return prot, spec
 

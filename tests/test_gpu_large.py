@@ -3,10 +3,10 @@ N/Q-deamidation <= 1, dF 0.02 Da, top-10) at full index size, and the
 serving recipe's spectra on the same index, sampled against the oracle.
 
 The oracle digests the whole database on one core before it can find a
-window (minutes), and a +-500 Da window of this database takes it minutes
-per spectrum, so the sampled spectra are searched by oracle processes in
-parallel (spawned, so no process forks after the GPU is in use), and the
-module runs only with HICOPS_LARGE=1."""
+window (minutes) and needs minutes per +-500 Da spectrum of this database,
+so one spawned oracle process (no fork after the GPU is in use) searches the
+sampled spectra while the GPU runs, and the module runs only with
+HICOPS_LARGE=1."""
 import concurrent.futures as cf
 import multiprocessing as mp
 import os
@@ -23,16 +23,21 @@ pytestmark = [pytest.mark.gpu, pytest.mark.slow,
               pytest.mark.skipif(os.environ.get("HICOPS_LARGE") != "1", reason="set HICOPS_LARGE=1")]
 
 
-def _oracle_one(workload_name, n_spectra, q):
-    """(in a spawned process) the oracle's result for spectrum q of the
-    workload's first n_spectra spectra on the open_large database."""
+def _oracle_all(jobs):
+    """(in one spawned process: the oracle holds about 340 B per peptide, so
+    one copy of the 237M-entry database is all the host takes) the oracle's
+    results for spectra q of the workloads' first n_spectra spectra."""
     import oracle
     oracle.build()
-    w = configs.BY_NAME[workload_name].with_spectra(n_spectra)
-    prot = synth.make_proteome(w.n_proteins, w.seed, w.protein_len)
-    spec = synth.make_spectra(prot, w)
-    db = oracle.OracleDb(prot.seq, prot.off, w.mods, w.params)
-    return db.search(spec, sel=np.array([q], dtype=np.uint32))
+    w0 = configs.BY_NAME[jobs[0][0]]
+    prot = synth.make_proteome(w0.n_proteins, w0.db_seed, w0.protein_len)
+    db = oracle.OracleDb(prot.seq, prot.off, w0.mods, w0.params)
+    out = []
+    for name, n_spectra, q in jobs:
+        w = configs.BY_NAME[name].with_spectra(n_spectra)
+        spec = synth.make_spectra(prot, w)
+        out.append(db.search(spec, sel=np.array([q], dtype=np.uint32)))
+    return out
 
 
 def test_open_large_and_serving_recipe_sampled(oracle_lib):
@@ -44,7 +49,7 @@ def test_open_large_and_serving_recipe_sampled(oracle_lib):
     pkg_build.build()
     wl = configs.OPEN_LARGE.with_spectra(20000)
     ws = configs.SERVING_STREAM.with_spectra(4096)
-    prot = synth.make_proteome(wl.n_proteins, wl.seed, wl.protein_len)
+    prot = synth.make_proteome(wl.n_proteins, wl.db_seed, wl.protein_len)
     spec_l = synth.make_spectra(prot, wl)
     spec_s = synth.make_spectra(prot, ws)
     npk = np.diff(spec_s.peak_off.astype(np.int64))
@@ -52,15 +57,16 @@ def test_open_large_and_serving_recipe_sampled(oracle_lib):
     l_sel = [0, 19999]
     jobs = [("open_large", wl.spectra.n_spectra, q) for q in l_sel] + \
            [("serving_stream", ws.spectra.n_spectra, q) for q in s_sel]
-    with cf.ProcessPoolExecutor(len(jobs), mp_context=mp.get_context("spawn")) as ex:
-        futs = [ex.submit(_oracle_one, *j) for j in jobs]
+    with cf.ProcessPoolExecutor(1, mp_context=mp.get_context("spawn")) as ex:
+        fut = ex.submit(_oracle_all, jobs)
         idx = hc.Index(prot.seq, prot.off, wl.mods, wl.params)
         st = idx.stats()
         got_l = idx.search(spec_l)                       # one batch of 20k spectra
         server = hc.Server(idx)
         got_s = server.poll(server.submit(spec_s), -1)   # the serving path
         server.close()
-        refs = [f.result() for f in futs]
+        del idx
+        refs = fut.result()
     assert st.n_peptides > 100_000_000
     for i, q in enumerate(l_sel):
         sel = np.array([q], dtype=np.uint32)

@@ -25,7 +25,7 @@ def gpu():
 
 
 def build_both(oracle_lib, w):
-    prot = synth.make_proteome(w.n_proteins, w.seed, w.protein_len)
+    prot = synth.make_proteome(w.n_proteins, w.db_seed, w.protein_len)
     idx = hc.Index(prot.seq, prot.off, w.mods, w.params)
     db = oracle_lib.OracleDb(prot.seq, prot.off, w.mods, w.params)
     return prot, idx, db
