@@ -752,13 +752,13 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel
             const uint32_t words = ((e - c) << kChunkShift) >> 5;
             const uint32_t nc = e, ne = min(e + m, col_end);
             const bool more = nc < col_end;
-            if (more) {                                   // next super-chunk's bounds, into L2
-                load_runs(nc, ne);
-                prefetch_runs();
-            }
+            if (more) load_runs(nc, ne);                 // next super-chunk's bounds: in flight during pass A
             pass_a(buf, cbase, x0, x1, par);
             uint32_t excl = 0;
-            if (more) excl = scan_runs_1<PPT>(sh, nnorm, ppt, ra, rb);
+            if (more) {                                   // its runs into L2 while this one finishes
+                prefetch_runs();
+                excl = scan_runs_1<PPT>(sh, nnorm, ppt, ra, rb);
+            }
             if (R > log_dirty) log_dirty = R;
             __syncthreads();
             const uint32_t ncand = sh.ncand[par];
