@@ -136,7 +136,7 @@ uint32_t max_segments(const hicops_search_config& c, uint32_t n) {
 template <int KMAX, int THREADS>
 hicops_status launch_search_t(const SearchArgs& sa, uint32_t ctas_per_sm, uint64_t max_units, cudaStream_t s) {
     static int occ = -1;
-    const size_t smem = sizeof(uint32_t) * kChunk;   // 64 KB: the kernel's counters / bit-planes / slots
+    const size_t smem = sizeof(uint32_t) * kDynWords;   // 68 KB: the kernel's planes, log, slots / counters
     if (occ < 0) {
         HC_CUDA(cudaFuncSetAttribute(search_kernel<KMAX, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
@@ -448,7 +448,7 @@ extern "C" hicops_status hicops_autotune(hicops_index* idx, const hicops_batch* 
     if (st != HICOPS_OK) return st;
     if (!b->on_device || b->n == 0) { set_error("autotune needs a non-empty device batch"); return HICOPS_EINVAL; }
     const uint32_t cand_threads[2] = {256, 512};
-    const uint32_t cand_cm[4] = {2, 3, 4, 5};   // chunk_entries
+    const uint32_t cand_cm[4] = {3, 4, 5, 6};   // chunk_entries
     const uint32_t cand_ctas[2] = {0, 1};
     const uint32_t cand_seg[3] = {0, 1u << 18, 1u << 16};
     cudaStream_t s = (cudaStream_t)b->cuda_stream;

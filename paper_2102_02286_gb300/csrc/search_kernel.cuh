@@ -14,7 +14,7 @@
 //           prefix sum; lane l of a warp takes entries l, l + 32, ...) sets
 //           the peptide's bit in a "seen" bit-plane and, when it was set, in
 //           a "twice" plane (shared-memory atomicOr), and is logged in shared
-//           memory as (peptide offset << 1 | isY | peak << 18); first bits
+//           memory as (peptide offset << 1 | isY | peak << 19); first bits
 //           set in the twice plane are counted;
 //   mark    only when nslices >= min_shared - 1 (peptides seen once with
 //           enough hot bits are candidates too) or when there are more than
@@ -30,26 +30,29 @@
 //           bucket bitmaps; peptides with nb + ny >= min_shared are ranked
 //           with the exact key K = LF[nb] + LF[ny] + LS[S] into the thread's
 //           top-k and the shared histogram.
-// A super-chunk with more than kMaxEntries entries is searched column by
-// column with 16384 directly indexed counters, and so is every column of a
-// unit whose spectrum has >= min_shared hot peaks (bitmaps alone can qualify
-// a peptide; that epilogue scans every counter and the bitmaps).
+// The planes take 2 x 512 words per column of the super-chunk and the log
+// the words after them, so sparse spectra get wide super-chunks and dense
+// ones long logs.  A super-chunk whose planes and log do not fit is searched
+// column by column with 16384 directly indexed counters, and so is every
+// column of a unit whose spectrum has >= min_shared hot peaks (bitmaps alone
+// can qualify a peptide; that epilogue scans every counter and the bitmaps).
 
 constexpr int kMaxHot = 6;                 // bitmap slices (b or y bitmap of a hot bucket) per spectrum
 constexpr int kMaxWarps = 16;              // CTAs of up to 512 threads
 constexpr int kTouchCap = 4096;            // touched list of a direct-counter column
-constexpr uint32_t kMaxCols = 8;           // widest super-chunk (columns of kChunk ids)
-constexpr uint32_t kPlaneWords = kMaxCols * kChunk / 32;   // 4096 words per bit-plane
-constexpr uint32_t kMaxEntries = 6144;     // log capacity (entries of one super-chunk)
+constexpr uint32_t kMaxCols = 12;          // widest super-chunk (columns of kChunk ids)
 constexpr uint32_t kSlots = 1024;          // candidate counters per round
 constexpr uint32_t kRound = 768;           // candidates per round (+31 at most)
-constexpr uint32_t kMaxRounds = kMaxEntries / kRound + 2;
-// 64 KB of dynamic shared memory, in 32-bit words:
-//   [0, 4096) seen plane | [4096, 8192) twice plane | [8192, 14336) log |
-//   [14336, 16384) kSlots 64-bit slots;  or 16384 direct counters
-constexpr uint32_t kLogWord = 2 * kPlaneWords;
-constexpr uint32_t kSlotWord = kLogWord + kMaxEntries;
-static_assert(kSlotWord + 2 * kSlots == kChunk, "shared-memory layout must fill 64 KB");
+// 68 KB of dynamic shared memory, in 32-bit words; a super-chunk of m columns
+// (W = 512 m words per plane):
+//   [0, W) seen plane | [W, 2W) twice plane | [2W, 2W + R) log |
+//   [kListWord, kSlotWord) slot compaction lists | [kSlotWord, kDynWords) kSlots 64-bit slots;
+// or [0, 16384) direct counters (over lists and slots, which are zero then)
+constexpr uint32_t kDynWords = kChunk + 1024;
+constexpr uint32_t kSlotWord = kDynWords - 2 * kSlots;
+constexpr uint32_t kListWord = kSlotWord - kSlots;
+constexpr uint32_t kMaxRounds = kListWord / kRound + 2;
+static_assert(2 * kMaxCols * kChunk / 32 < kListWord, "planes of the widest super-chunk leave room for a log");
 
 struct SearchArgs {
     const uint32_t* qbin;
@@ -233,20 +236,18 @@ __device__ __forceinline__ void scan_runs_2(SearchShared& sh, int buf, int nnorm
 
 template <int KMAX, int THREADS>
 __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel(SearchArgs a) {
-    extern __shared__ __align__(16) uint32_t smem32[];   // 16384 words (layout above)
+    extern __shared__ __align__(16) uint32_t smem32[];   // kDynWords words (layout above)
     uint32_t* const cnt = smem32;
     uint32_t* const seen = smem32;
-    uint32_t* const twice = smem32 + kPlaneWords;
-    uint32_t* const logw = smem32 + kLogWord;
+    uint32_t* const lists = smem32 + kListWord;
     unsigned long long* const tab = reinterpret_cast<unsigned long long*>(smem32 + kSlotWord);
     __shared__ SearchShared sh;
     constexpr int nwarps = THREADS / 32;
     constexpr int PPT = kMaxTopN / THREADS;             // ordinary peaks per thread (at most)
-    constexpr int WPT = kPlaneWords / THREADS;          // plane words per thread
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const uint32_t last_col = a.skip_stride - 1;
-    for (int i = tid; i < (int)kChunk; i += THREADS) smem32[i] = 0u;
+    for (int i = tid; i < (int)kDynWords; i += THREADS) smem32[i] = 0u;
     for (int i = tid; i < (int)kHistBins; i += THREADS) sh.hist[i] = 0;
     for (int i = tid; i <= (int)kMaxLen; i += THREADS) sh.lf[i] = a.lf[i];
     if (tid == 0) { sh.ncand[0] = 0u; sh.ncand[1] = 0u; }
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel
     const int k = (int)a.k;
     const uint32_t min_shared = a.min_shared;
     int par = 0;                  // alternates per super-chunk: which ncand counts
-    uint32_t log_dirty = 0;       // log words that may be non-zero
+    uint32_t log_lo = kListWord, log_dirty = 0;   // words [log_lo, log_dirty) may hold log records
     __syncthreads();
     for (;;) {
         if (tid == 0) {
@@ -363,8 +364,12 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel
             for (int w = 0; w < nwarps; ++w) total += sh.wsum[w];
             const uint32_t ncols = col_end - col_lo;
             if (!hot_alone) {
-                const uint32_t target = min(a.target_entries, kMaxEntries);
-                uint64_t want = total ? ((uint64_t)target * ncols) / total : ncols;
+                // about target_entries entries, and planes (1024 words a
+                // column) plus 1.25 times the mean log within kListWord
+                // words, so that denser-than-mean super-chunks still fit
+                uint64_t want = total ? ((uint64_t)a.target_entries * ncols) / total : ncols;
+                const uint64_t fit = (uint64_t)kListWord * ncols / ((uint64_t)1024 * ncols + total + total / 4);
+                if (want > fit) want = fit;
                 if (want < 1) want = 1;
                 if (want > kMaxCols) want = kMaxCols;
                 m = min((uint32_t)want, ncols);
@@ -373,6 +378,8 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel
         }
         TopK<KMAX> top;
         top.init();
+        uint32_t* twice = smem32;   // the current super-chunk's twice plane and log
+        uint32_t* logw = smem32;
 
         // Calls fn(f, entry, peak) for every entry f of parity buffer buf.
         // Warp w takes a contiguous share; lane l takes f0 + l + 32 j, kJ
@@ -502,8 +509,8 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel
         // for_each_entry, specialised): per batch of kJ entries a lane first
         // issues all its loads, then all its seen-plane atomics, then the
         // twice-plane atomics of the second hits, so the latencies overlap.
-        // A log record is (entry - 2 cb) | peak << 18, i.e. offset << 1 |
-        // isY in bits 0..17.
+        // A log record is (entry - 2 cb) | peak << 19, i.e. offset << 1 |
+        // isY in bits 0..18.
         auto pass_a = [&](int buf, uint32_t cb, uint32_t x0, uint32_t x1, int par) {
             constexpr int kJ = 8;
             const uint32_t R = sh.pre[buf][nnorm];
@@ -514,7 +521,7 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel
                 int li = sh.wli[buf][warp];
                 uint32_t nxt = sh.pre[buf][li + 1];
                 const uint32_t* gp = a.entry + (sh.pbase[li] + sh.rs[buf][li] - sh.pre[buf][li]);
-                uint32_t lsh = (uint32_t)li << 18;
+                uint32_t lsh = (uint32_t)li << 19;
                 const uint32_t e_lo = x0 << 1, e_hi = x1 << 1, e_cb = cb << 1;   // entries of pids in [x0, x1)
                 for (uint32_t fb = f0 + lane; fb < f1; fb += 32 * kJ) {
                     uint32_t ev[kJ], lr[kJ];
@@ -528,7 +535,7 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel
                                 ++li;
                                 nxt = sh.pre[buf][li + 1];
                                 gp = a.entry + (sh.pbase[li] + sh.rs[buf][li] - sh.pre[buf][li]);
-                                lsh = (uint32_t)li << 18;
+                                lsh = (uint32_t)li << 19;
                             }
                             lr[j] = lsh;
                             ev[j] = __ldg(gp + f);
@@ -635,13 +642,13 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel
                 }
 #pragma unroll
                 for (int u = 0; u < kU; ++u)
-                    tw[u] = rec[u] != 0xffffffffu ? twice[(rec[u] & 0x3ffffu) >> 6] : 0u;
+                    tw[u] = rec[u] != 0xffffffffu ? twice[(rec[u] & 0x7ffffu) >> 6] : 0u;
 #pragma unroll
                 for (int u = 0; u < kU; ++u) {
-                    const uint32_t off = (rec[u] & 0x3ffffu) >> 1;
+                    const uint32_t off = (rec[u] & 0x7ffffu) >> 1;
                     const uint32_t w = off >> 5;
                     if (rec[u] == 0xffffffffu || !((tw[u] >> (off & 31)) & 1u) || w < wlo || w >= whi) continue;
-                    const uint32_t v = counter_inc_y(rec[u] & 1u, sh.pinc[rec[u] >> 18]);
+                    const uint32_t v = counter_inc_y(rec[u] & 1u, sh.pinc[rec[u] >> 19]);
                     const unsigned long long item = ((unsigned long long)off << 32) | v;
                     uint32_t sl = slot_of(off);
                     for (uint32_t probe = 0; probe < kSlots; ++probe) {
@@ -654,9 +661,8 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel
             }
         };
         // Visits the occupied slots.  Warp w compacts the occupied slot
-        // indices of its share [w * spw, (w + 1) * spw) into the same words
-        // of the seen plane (free once pass A is over), visits them with all
-        // lanes, and zeroes the slots and those plane words.
+        // indices of its share [w * spw, (w + 1) * spw) into its list words,
+        // visits them with all lanes, and zeroes the slots and the list.
         auto slots_epilogue = [&](uint32_t cb) {
             constexpr uint32_t spw = kSlots / nwarps;
             const uint32_t base = (uint32_t)warp * spw;
@@ -666,19 +672,19 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel
                 const uint32_t sl = base + i0 + lane;
                 const bool occ = tab[sl] != 0ull;
                 const unsigned msk = __ballot_sync(0xffffffffu, occ);
-                if (occ) seen[base + cnt + __popc(msk & lt)] = sl;
+                if (occ) lists[base + cnt + __popc(msk & lt)] = sl;
                 cnt += __popc(msk);
             }
             __syncwarp();
             for (uint32_t i = lane; i < cnt; i += 32) {
-                const uint32_t sl = seen[base + i];
+                const uint32_t sl = lists[base + i];
                 const unsigned long long v = tab[sl];
                 tab[sl] = 0ull;
                 visit((uint32_t)v, cb + (uint32_t)(v >> 32));
             }
             __syncwarp();
 #pragma unroll
-            for (uint32_t i0 = 0; i0 < spw; i0 += 32) seen[base + i0 + lane] = 0u;
+            for (uint32_t i0 = 0; i0 < spw; i0 += 32) lists[base + i0 + lane] = 0u;
         };
         // zeroes plane words [w0, w1), both multiples of 4
         auto clear_words = [&](uint32_t* plane, uint32_t w0, uint32_t w1) {
@@ -713,13 +719,18 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel
         __syncthreads();
         while (c < col_end) {
             const uint32_t R = sh.pre[buf][nnorm];
-            if (hot_alone || R > kMaxEntries) {
-                // column by column with direct counters, which cover the log
-                if (log_dirty) {
-                    for (uint32_t i = tid; i < log_dirty; i += THREADS) logw[i] = 0u;
-                    log_dirty = 0;
-                    __syncthreads();
-                }
+            const uint32_t words = ((e - c) << kChunkShift) >> 5;
+            const bool direct = hot_alone || 2 * words + R > kListWord;
+            // words [log_lo, log_dirty) may hold old log records: clear them
+            // before they become counters or this super-chunk's planes
+            if (log_dirty > log_lo && (direct || 2 * words > log_lo)) {
+                for (uint32_t i = log_lo + tid; i < log_dirty; i += THREADS) smem32[i] = 0u;
+                log_lo = kListWord;
+                log_dirty = 0;
+                __syncthreads();
+            }
+            if (direct) {
+                // column by column with direct counters
                 if (e - c == 1) {
                     const uint32_t cb = c << kChunkShift;
                     column_pass(buf, cb, max(seg_lo, cb), min(seg_hi, cb + kChunk));
@@ -749,7 +760,8 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel
             }
             const uint32_t cbase = c << kChunkShift;
             const uint32_t x0 = max(seg_lo, cbase), x1 = min(seg_hi, e << kChunkShift);
-            const uint32_t words = ((e - c) << kChunkShift) >> 5;
+            twice = seen + words;
+            logw = seen + 2 * words;
             const uint32_t nc = e, ne = min(e + m, col_end);
             const bool more = nc < col_end;
             if (more) load_runs(nc, ne);                 // next super-chunk's bounds: in flight during pass A
@@ -759,7 +771,8 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel
                 prefetch_runs();
                 excl = scan_runs_1<PPT>(sh, nnorm, ppt, ra, rb);
             }
-            if (R > log_dirty) log_dirty = R;
+            if (2 * words < log_lo) log_lo = 2 * words;
+            if (2 * words + R > log_dirty) log_dirty = 2 * words + R;
             __syncthreads();
             const uint32_t ncand = sh.ncand[par];
             if (tid == 0) sh.ncand[par ^ 1] = 0u;         // the next super-chunk's count
@@ -778,8 +791,8 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel
             } else if (ncand) {
                 replay(R, 0u, words);
                 __syncthreads();
-                slots_epilogue(cbase);                    // zeroes seen words [0, kSlots)
-                clear_words(seen, kSlots, words);
+                slots_epilogue(cbase);
+                clear_words(seen, 0u, words);
                 clear_words(twice, 0u, words);
             } else {
                 clear_words(seen, 0u, words);             // the twice plane is empty
