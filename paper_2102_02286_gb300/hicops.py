@@ -90,9 +90,6 @@ PSM_DTYPE = np.dtype([("query", np.uint32), ("pid", np.uint32), ("nb", np.uint8)
 assert PSM_DTYPE.itemsize == 32
 
 _lib = None
-EXPORTS = ["hicops_digest", "hicops_index_upload", "hicops_build_index", "hicops_search",
-           "hicops_search_work", "hicops_index_get_stats", "hicops_peptide", "hicops_index_copy_csr",
-           "hicops_index_free", "hicops_last_error"]
 
 
 def lib_path() -> str:
