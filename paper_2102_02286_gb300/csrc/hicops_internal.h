@@ -23,9 +23,9 @@ constexpr uint32_t kMaxTopN = 1024;
 // stores where each chunk starts (the skip table).
 constexpr uint32_t kChunkShift = 14;
 constexpr uint32_t kChunk = 1u << kChunkShift;
-// A bucket holding at least P >> kHotShift entries (1/32 of the database)
+// A bucket holding at least P >> kHotShift entries (1/64 of the database)
 // is also stored as a pid bitmap.
-constexpr uint32_t kHotShift = 5;
+constexpr uint32_t kHotShift = 6;
 
 // Counter packing for one (spectrum, peptide) pair, 32 bits:
 //   bits 26..31 nb, bits 20..25 ny, bits 0..19 S (sum of quantised intensity).
