@@ -206,7 +206,7 @@ hicops_status enqueue_search(hicops_index* idx, const DevBatch& d, uint32_t n, c
     if (st != HICOPS_OK) return st;
     mark(idx, 3, s, timing_marks);
     MergeArgs ma{w.seg_off, w.utop, d_hist, n, k, 0, d_psm, idx->pid_stride, idx->pid_base};
-    merge_kernel<<<n, kMergeThreads, 0, s>>>(ma);
+    merge_kernel<<<(n + kMergeWarps - 1) / kMergeWarps, kMergeWarps * 32, 0, s>>>(ma);
     count_launches(1);
     HC_CUDA(cudaGetLastError());
     mark(idx, 4, s, timing_marks);
@@ -719,7 +719,7 @@ extern "C" hicops_status hicops_merge_shards(uint32_t n_shards, uint32_t n, uint
         count_launches(1);
         HC_CUDA(cudaGetLastError());
         MergeArgs ma{seg_off, utop, d_hist, n, top_k, 0, d_out, 1u, 0u};
-        merge_kernel<<<n, kMergeThreads, 0, s>>>(ma);
+        merge_kernel<<<(n + kMergeWarps - 1) / kMergeWarps, kMergeWarps * 32, 0, s>>>(ma);
         count_launches(1);
         HC_CUDA(cudaGetLastError());
         if (!on_device) {

@@ -15,8 +15,7 @@ constexpr int kPrepThreads = 256;
 constexpr int kSearchThreads = 256;
 constexpr int kMinSegPids = (int)kChunk;  // smallest segment of a split window
 constexpr int kMaxSegs = 64;              // most segments a window is split into
-constexpr int kMergeThreads = 256;
-constexpr uint16_t kNoIdx = 0xffff;       // padding slot of the merge sort
+constexpr int kMergeWarps = 8;          // spectra per merge block
 
 struct UnitTop {
     int64_t key;
@@ -187,106 +186,112 @@ struct MergeArgs {
     uint32_t pid_stride, pid_base;   // row pid = list pid * pid_stride + pid_base
 };
 
-__device__ __forceinline__ double block_sum(double v, double* red) {
+__device__ __forceinline__ double warp_sum_f64(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) red[w] = v;
-    __syncthreads();
-    double t = 0;
-    for (int i = 0; i < (int)(blockDim.x / 32); ++i) t += red[i];
-    return t;
+    return v;
 }
 
-// one block per spectrum: merge the segment lists, then the e-value fit
-__global__ void __launch_bounds__(kMergeThreads) merge_kernel(MergeArgs a) {
-    __shared__ UnitTop buf[kMaxSegs * kMaxTopK];
-    __shared__ uint16_t sk[kMaxSegs * kMaxTopK];
-    __shared__ uint32_t suf[kHistBins];
-    __shared__ double red[kMergeThreads / 32];
-    __shared__ uint32_t s_mode;
-    const uint32_t q = blockIdx.x;
+// One warp per spectrum (kMergeWarps spectra per block): the top-k merge of
+// the spectrum's unit lists, then the e-value fit (Supplementary Algorithm
+// 4) over its histogram.  Lane l owns unit lists l and l + 32 (at most 64
+// units, each sorted by (key desc, pid asc)); k rounds of a warp argmax
+// over the list heads give the rows in rank order.  Lane l holds histogram
+// bins 8l .. 8l + 7.
+__global__ void __launch_bounds__(kMergeWarps * 32) merge_kernel(MergeArgs a) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t q = blockIdx.x * kMergeWarps + (threadIdx.x >> 5);
+    if (q >= a.n) return;
     const uint32_t k = a.k;
-    const uint64_t u0 = a.seg_off[q], u1 = a.seg_off[q + 1];
-    const int nseg = (int)(u1 - u0);
-    const int m = nseg * (int)k;
-    // sort (key desc, pid asc) by sorting an index-tagged 64-bit rank
-    const int npow = next_pow2(m > 0 ? m : 1);
-    for (int i = threadIdx.x; i < npow; i += blockDim.x) {
-        if (i < m) {
-            buf[i] = a.utop[u0 * k + i];
-            sk[i] = (uint16_t)i;
-        } else {
-            sk[i] = kNoIdx;
+    const uint64_t u0 = a.seg_off[q];
+    const int nseg = (int)(a.seg_off[q + 1] - u0);
+    const UnitTop* lists = a.utop + u0 * k;
+    uint32_t h0 = 0, h1 = 0;   // heads of lists lane and lane + 32
+    UnitTop row;               // row `lane` of the result
+    row.key = INT64_MIN;
+    row.pid = 0xffffffffu;
+    row.packed = 0u;
+    for (uint32_t r = 0; r < k; ++r) {
+        int64_t bk = INT64_MIN;
+        uint32_t bp = 0xffffffffu, bpk = 0u;
+        int which = -1;
+        if (lane < nseg && h0 < k) {
+            const UnitTop t = lists[(uint64_t)lane * k + h0];
+            if (t.pid != 0xffffffffu) { bk = t.key; bp = t.pid; bpk = t.packed; which = 0; }
         }
-    }
-    __syncthreads();
-    // odd-even by comparator over buf via index sort (bitonic on indices)
-    for (int kk = 2; kk <= npow; kk <<= 1) {
-        for (int j = kk >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < npow; i += blockDim.x) {
-                const int ixj = i ^ j;
-                if (ixj > i) {
-                    const uint16_t x = sk[i], y = sk[ixj];
-                    // "x after y" in (key desc, pid asc) order; padding last
-                    bool x_after;
-                    if (x == kNoIdx) x_after = (y != kNoIdx);
-                    else if (y == kNoIdx) x_after = false;
-                    else x_after = better(buf[y].key, buf[y].pid, buf[x].key, buf[x].pid);
-                    const bool up = (i & kk) == 0;
-                    if (x_after == up) { sk[i] = y; sk[ixj] = x; }
-                }
-            }
-            __syncthreads();
+        if (lane + 32 < nseg && h1 < k) {
+            const UnitTop t = lists[(uint64_t)(lane + 32) * k + h1];
+            if (t.pid != 0xffffffffu && better(t.key, t.pid, bk, bp)) { bk = t.key; bp = t.pid; bpk = t.packed; which = 1; }
         }
-    }
-    // survival function and fit over the histogram
-    const uint32_t* h = a.hist + (uint64_t)q * kHistBins;
-    const int j = threadIdx.x;   // one bin per thread (256 threads)
-    const uint32_t hv = h[j];
-    // suffix sums
-    suf[j] = hv;
-    __syncthreads();
-    for (int o = 1; o < (int)kHistBins; o <<= 1) {
-        const uint32_t add = (j + o < (int)kHistBins) ? suf[j + o] : 0u;
-        __syncthreads();
-        suf[j] += add;
-        __syncthreads();
-    }
-    // mode: highest count, lowest bin on ties
-    if (j == 0) s_mode = 0;
-    __syncthreads();
-    {
-        const uint64_t v = ((uint64_t)hv << 32) | (uint32_t)(255 - j);
-        uint64_t best = v;
+        int64_t wk = bk;
+        uint32_t wp = bp, wpk = bpk;
+        int wl = lane;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const uint64_t ov = __shfl_xor_sync(0xffffffffu, best, o);
-            if (ov > best) best = ov;
+            const int64_t ok = __shfl_xor_sync(0xffffffffu, wk, o);
+            const uint32_t op = __shfl_xor_sync(0xffffffffu, wp, o);
+            const uint32_t opk = __shfl_xor_sync(0xffffffffu, wpk, o);
+            const int ol = __shfl_xor_sync(0xffffffffu, wl, o);
+            if (better(ok, op, wk, wp) || (ok == wk && op == wp && ol < wl)) { wk = ok; wp = op; wpk = opk; wl = ol; }
         }
-        __shared__ uint64_t wbest[kMergeThreads / 32];
-        if ((j & 31) == 0) wbest[j >> 5] = best;
-        __syncthreads();
-        if (j == 0) {
-            uint64_t b = wbest[0];
-            for (int w = 1; w < kMergeThreads / 32; ++w) if (wbest[w] > b) b = wbest[w];
-            s_mode = 255 - (uint32_t)(b & 0xffffffffu);
-        }
-        __syncthreads();
+        if (wp != 0xffffffffu && lane == wl) { if (which == 0) ++h0; else ++h1; }
+        if ((uint32_t)lane == r) { row.key = wk; row.pid = wp; row.packed = wpk; }
     }
-    const double N = (double)suf[0];
-    const bool have_top = m > 0 && sk[0] != kNoIdx && buf[sk[0]].pid != 0xffffffffu;
+    // survival function of the histogram: suf[j] = sum of hist[i >= j]
+    const uint32_t* hq = a.hist + (uint64_t)q * kHistBins + 8 * lane;   // caller's buffer: 4-byte aligned only
+    uint32_t v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = hq[i];
+    uint32_t loc[8];
+    uint32_t run = 0;
+#pragma unroll
+    for (int i = 7; i >= 0; --i) { run += v[i]; loc[i] = run; }
+    uint32_t above = run;   // inclusive suffix over lanes >= lane
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_down_sync(0xffffffffu, above, o);
+        if (lane + o < 32) above += y;
+    }
+    const double N = (double)__shfl_sync(0xffffffffu, above, 0);
+    above -= run;           // lanes > lane
+    // mode: the highest count, the lowest bin on ties
+    uint64_t best = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const uint64_t c = ((uint64_t)v[i] << 32) | (uint32_t)(255 - (8 * lane + i));
+        if (c > best) best = c;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t ob = __shfl_xor_sync(0xffffffffu, best, o);
+        if (ob > best) best = ob;
+    }
+    const int mode = 255 - (int)(best & 0xffffffffu);
+    const int64_t key0 = __shfl_sync(0xffffffffu, row.key, 0);
+    const uint32_t pid0 = __shfl_sync(0xffffffffu, row.pid, 0);
+    const bool have_top = pid0 != 0xffffffffu;
     int64_t jtop = 0;
-    if (have_top) { jtop = buf[sk[0]].key >> 31; if (jtop > 255) jtop = 255; }
-    const bool pt = have_top && j >= (int)s_mode + 1 && j <= jtop - 1 && suf[j] > 0;
-    const double x = (double)j;
-    const double y = pt ? log10((double)suf[j] / N) : 0.0;
-    const double cn = block_sum(pt ? 1.0 : 0.0, red);
-    const double sx = block_sum(pt ? x : 0.0, red);
-    const double sy = block_sum(pt ? y : 0.0, red);
-    const double sxx = block_sum(pt ? x * x : 0.0, red);
-    const double sxy = block_sum(pt ? x * y : 0.0, red);
+    if (have_top) { jtop = key0 >> 31; if (jtop > 255) jtop = 255; }
+    double cn = 0, sx = 0, sy = 0, sxx = 0, sxy = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int j = 8 * lane + i;
+        const uint32_t sj = loc[i] + above;
+        if (have_top && j >= mode + 1 && j <= jtop - 1 && sj > 0) {
+            const double x = (double)j;
+            const double y = log10((double)sj / N);
+            cn += 1.0;
+            sx += x;
+            sy += y;
+            sxx += x * x;
+            sxy += x * y;
+        }
+    }
+    cn = warp_sum_f64(cn);
+    sx = warp_sum_f64(sx);
+    sy = warp_sum_f64(sy);
+    sxx = warp_sum_f64(sxx);
+    sxy = warp_sum_f64(sxy);
     const bool fit = cn >= 3.0;
     double wfit = 0.0, bfit = 0.0;
     if (fit) {
@@ -294,20 +299,17 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(MergeArgs a) {
         wfit = (cn * sxy - sx * sy) / den;
         bfit = (sy - wfit * sx) / cn;
     }
-    for (uint32_t r = threadIdx.x; r < k; r += blockDim.x) {
+    if ((uint32_t)lane < k) {
         hicops_psm o;
         o.query = a.q_base + q;
         o.reserved = 0;
-        const bool real = (int)r < m && sk[r] != kNoIdx && buf[sk[r]].pid != 0xffffffffu;
-        if (real) {
-            const UnitTop t = buf[sk[r]];
-            o.pid = t.pid * a.pid_stride + a.pid_base;
-            o.nb = (uint8_t)(t.packed >> kNbShift);
-            o.ny = (uint8_t)((t.packed >> kNyShift) & 63u);
-            o.key = t.key;
-            o.hyperscore = (float)((double)t.key * 0x1p-32);
-            if (fit) o.evalue = N * exp10(wfit * ((double)t.key * 0x1p-31) + bfit);
-            else o.evalue = N;
+        if (row.pid != 0xffffffffu) {
+            o.pid = row.pid * a.pid_stride + a.pid_base;
+            o.nb = (uint8_t)(row.packed >> kNbShift);
+            o.ny = (uint8_t)((row.packed >> kNyShift) & 63u);
+            o.key = row.key;
+            o.hyperscore = (float)((double)row.key * 0x1p-32);
+            o.evalue = fit ? N * exp10(wfit * ((double)row.key * 0x1p-31) + bfit) : N;
         } else {
             o.pid = 0xffffffffu;
             o.nb = o.ny = 0;
@@ -315,7 +317,7 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(MergeArgs a) {
             o.hyperscore = 0.0f;
             o.evalue = INFINITY;
         }
-        a.out[(uint64_t)q * k + r] = o;
+        a.out[(uint64_t)q * k + lane] = o;
     }
 }
 
