@@ -150,9 +150,10 @@ def search_traffic_record():
 
 
 def search_source_hash() -> str:
-    """sha256 over the search kernel's sources (the host side and the kernels)."""
+    """sha256 over the sources that decide the search kernel's memory traffic:
+    the kernel itself, the index layout and its constants."""
     h = hashlib.sha256()
-    for name in ("search.cu", "search_kernels.cuh", "search_kernel.cuh"):
+    for name in ("search_kernel.cuh", "hicops_internal.h", "index_build.cu"):
         with open(os.path.join(ROOT, "paper_2102_02286_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
