@@ -184,8 +184,9 @@ hicops_status enqueue_search(hicops_index* idx, const DevBatch& d, uint32_t n, c
     mark(idx, 0, s, timing_marks);
     PrepArgs pa{d.peak_off, d.mz, d.inten, d.prec, d.z, d.tol, n, p.top_n_peaks, p.bin_width_da, p.frag_mz_min,
                 p.frag_mz_max, (double)p.intensity_scale, di.mass, idx->mass.size(), w.qbin, w.qiq, w.qn, w.lo, w.hi};
-    prep_kernel<<<n, kPrepThreads, 0, s>>>(pa);
-    count_launches(1);
+    prep_warp_kernel<<<(n + kPrepWarps - 1) / kPrepWarps, kPrepWarps * 32, 0, s>>>(pa);
+    prep_kernel<<<n, kPrepThreads, 0, s>>>(pa);   // spectra of more than kPrepWarpPeaks peaks
+    count_launches(2);
     HC_CUDA(cudaGetLastError());
     mark(idx, 1, s, timing_marks);
     const uint32_t max_seg = w.max_seg;
@@ -343,8 +344,9 @@ extern "C" hicops_status hicops_search_work(hicops_index* idx, const hicops_batc
         PrepArgs pa{d.peak_off, d.mz, d.inten, d.prec, d.z, d.tol, n, p.top_n_peaks, p.bin_width_da,
                     p.frag_mz_min, p.frag_mz_max, (double)p.intensity_scale, idx->dev.mass, idx->mass.size(),
                     qbin, qiq, qn, lo, hi};
+        prep_warp_kernel<<<(n + kPrepWarps - 1) / kPrepWarps, kPrepWarps * 32, 0, s>>>(pa);
         prep_kernel<<<n, kPrepThreads, 0, s>>>(pa);
-        count_launches(1);
+        count_launches(2);
         HC_CUDA(cudaGetLastError());
         work_kernel<<<n, 256, 0, s>>>(qbin, qn, lo, hi, p.top_n_peaks, idx->dev.off, idx->dev.entry, hits);
         count_launches(1);

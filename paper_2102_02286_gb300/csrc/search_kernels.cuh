@@ -12,6 +12,8 @@ namespace hicops {
 namespace {
 
 constexpr int kPrepThreads = 256;
+constexpr int kPrepWarpPeaks = 256;        // spectra with at most this many raw peaks: one warp each
+constexpr int kPrepWarps = 8;              // spectra per block of prep_warp_kernel
 constexpr int kSearchThreads = 256;
 constexpr int kMinSegPids = (int)kChunk;  // smallest segment of a split window
 constexpr int kMaxSegs = 64;              // most segments a window is split into
@@ -81,6 +83,7 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(PrepArgs a) {
     const uint32_t q = blockIdx.x;
     const uint64_t p0 = a.peak_off[q], p1 = a.peak_off[q + 1];
     const uint64_t cnt = p1 >= p0 ? p1 - p0 : 0;
+    if (cnt <= (uint64_t)kPrepWarpPeaks) return;   // prep_warp_kernel's spectra
     const double prec = a.prec_mz[q];
     const double tol = a.tol[q];
     const uint32_t z = a.charge[q];
@@ -136,6 +139,105 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(PrepArgs a) {
     }
     valid = valid && keep > 0;
     if (threadIdx.x == 0) {
+        a.qn[q] = valid ? (uint32_t)keep : 0u;
+        uint32_t lo = 0, hi = 0;
+        if (valid) {
+            const double Mq = __dmul_rn(__dsub_rn(prec, kProtonDa), (double)z);
+            lo = (uint32_t)mass_bound(a.mass, a.P, __dsub_rn(Mq, tol), false);
+            hi = (uint32_t)mass_bound(a.mass, a.P, __dadd_rn(Mq, tol), true);
+        }
+        a.lo[q] = lo;
+        a.hi[q] = hi;
+    }
+}
+
+__device__ __forceinline__ void warp_bitonic_sort_u64(uint64_t* s, int npow, int lane) {
+    for (int k = 2; k <= npow; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = lane; i < npow; i += 32) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const uint64_t x = s[i], y = s[ixj];
+                    const bool up = (i & k) == 0;
+                    if ((x > y) == up) { s[i] = y; s[ixj] = x; }
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// prep_kernel's computation for spectra of at most kPrepWarpPeaks raw
+// peaks, one warp each, in a 2 KB slice of shared memory: the same keys and
+// sorts, so the same retained peaks, quantised intensities and window.
+__global__ void __launch_bounds__(kPrepWarps * 32) prep_warp_kernel(PrepArgs a) {
+    __shared__ uint64_t keys_all[kPrepWarps][kPrepWarpPeaks];
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    const uint32_t q = blockIdx.x * kPrepWarps + wi;
+    if (q >= a.n) return;
+    uint64_t* keys = keys_all[wi];
+    const uint64_t p0 = a.peak_off[q], p1 = a.peak_off[q + 1];
+    const uint64_t cnt = p1 >= p0 ? p1 - p0 : 0;
+    if (cnt > (uint64_t)kPrepWarpPeaks) return;   // prep_kernel's spectra
+    const double prec = a.prec_mz[q];
+    const double tol = a.tol[q];
+    const uint32_t z = a.charge[q];
+    bool valid = p1 >= p0 && z > 0 && isfinite(prec) && isfinite(tol) && tol >= 0.0;
+    int keep = 0;
+    if (valid && cnt > 0) {
+        const int npow = next_pow2((int)cnt);
+        for (int i = lane; i < npow; i += 32) {
+            uint64_t k = ~0ull;
+            if (i < (int)cnt) {
+                const float m = a.mz[p0 + i], I = a.inten[p0 + i];
+                const double md = (double)m;
+                if (isfinite(m) && isfinite(I) && I > 0.0f && md >= a.mz_lo && md < a.mz_hi) {
+                    const uint32_t bin = (uint32_t)floor(md / a.w);
+                    k = ((uint64_t)bin << 32) | __float_as_uint(I);
+                }
+            }
+            keys[i] = k;
+        }
+        __syncwarp();
+        warp_bitonic_sort_u64(keys, npow, lane);
+        // one representative per bin (the most intense), re-keyed by
+        // (intensity desc, bin asc) and compacted in place in index order
+        int nrep = 0;
+        for (int i0 = 0; i0 < npow; i0 += 32) {
+            const int i = i0 + lane;
+            uint64_t r = 0;
+            bool is_rep = false;
+            if (i < npow) {
+                const uint64_t k = keys[i];
+                if (k != ~0ull) {
+                    is_rep = (i + 1 == npow) || ((keys[i + 1] >> 32) != (k >> 32));
+                    r = ((uint64_t)(~(uint32_t)k) << 32) | (k >> 32);
+                }
+            }
+            const unsigned msk = __ballot_sync(0xffffffffu, is_rep);
+            __syncwarp();   // every read of this round before any write (writes land at indices <= i)
+            if (is_rep) keys[nrep + __popc(msk & ((1u << lane) - 1u))] = r;
+            nrep += __popc(msk);
+            __syncwarp();
+        }
+        const int npow2 = next_pow2(nrep > 0 ? nrep : 1);
+        for (int i = nrep + lane; i < npow2; i += 32) keys[i] = ~0ull;
+        __syncwarp();
+        warp_bitonic_sort_u64(keys, npow2, lane);
+        keep = nrep < (int)a.topn ? nrep : (int)a.topn;
+        if (keep > 0) {
+            const double Imax = (double)__uint_as_float(~(uint32_t)(keys[0] >> 32));
+            for (int t = lane; t < keep; t += 32) {
+                const uint64_t k = keys[t];
+                const double I = (double)__uint_as_float(~(uint32_t)(k >> 32));
+                const double r = floor(__dmul_rn(I, a.scale) / Imax);
+                a.qbin[(uint64_t)q * a.topn + t] = (uint32_t)k;
+                a.qiq[(uint64_t)q * a.topn + t] = r < 1.0 ? 1u : (uint32_t)r;
+            }
+        }
+    }
+    valid = valid && keep > 0;
+    if (lane == 0) {
         a.qn[q] = valid ? (uint32_t)keep : 0u;
         uint32_t lo = 0, hi = 0;
         if (valid) {
