@@ -110,7 +110,10 @@ hicops_status sm_count() {
 }
 
 hicops_status check_config(const hicops_search_config& c) {
-    if (c.threads != 0 && c.threads != 256 && c.threads != 512) { set_error("threads must be 256 or 512"); return HICOPS_EINVAL; }
+    if (c.threads != 0 && c.threads != 256 && c.threads != 384 && c.threads != 512) {
+        set_error("threads must be 256, 384 or 512");
+        return HICOPS_EINVAL;
+    }
     if (c.chunk_entries > 6) { set_error("chunk_entries must be in 1..6"); return HICOPS_EINVAL; }
     if (c.ctas_per_sm > 8) { set_error("ctas_per_sm must be <= 8"); return HICOPS_EINVAL; }
     return HICOPS_OK;
@@ -165,6 +168,7 @@ hicops_status launch_search_k(const SearchArgs& sa, uint32_t ctas_per_sm, uint64
 hicops_status launch_search(const SearchArgs& sa, const hicops_search_config& c, uint64_t max_units,
                             cudaStream_t s) {
     if (c.threads == 512) return launch_search_k<512>(sa, c.ctas_per_sm, max_units, s);
+    if (c.threads == 384) return launch_search_k<384>(sa, c.ctas_per_sm, max_units, s);
     return launch_search_k<256>(sa, c.ctas_per_sm, max_units, s);
 }
 
@@ -449,7 +453,7 @@ extern "C" hicops_status hicops_autotune(hicops_index* idx, const hicops_batch* 
     hicops_status st = check_batch(idx, b);
     if (st != HICOPS_OK) return st;
     if (!b->on_device || b->n == 0) { set_error("autotune needs a non-empty device batch"); return HICOPS_EINVAL; }
-    const uint32_t cand_threads[2] = {256, 512};
+    const uint32_t cand_threads[2] = {256, 384};
     const uint32_t cand_cm[4] = {3, 4, 5, 6};   // chunk_entries
     const uint32_t cand_ctas[2] = {0, 1};
     const uint32_t cand_seg[3] = {0, 1u << 18, 1u << 16};

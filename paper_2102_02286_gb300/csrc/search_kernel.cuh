@@ -28,8 +28,12 @@
 //           fewer than kSlots keys, so probing always ends;
 //   epilogue the occupied slots get the hot peaks' contributions from the
 //           bucket bitmaps; peptides with nb + ny >= min_shared are ranked
-//           with the exact key K = LF[nb] + LF[ny] + LS[S] into the thread's
-//           top-k and the shared histogram.
+//           with the exact key K = LF[nb] + LF[ny] + LS[S] and counted in the
+//           shared histogram; those better than their warp's k-th enter the
+//           warp's top-k list in shared memory (lanes take turns at points
+//           where the warp is converged), and the warps' lists are merged at
+//           the end of the unit.  Keeping the lists out of registers leaves
+//           80 registers a thread, so CTAs of 384 threads run two per SM.
 // The planes take 2 x 512 words per column of the super-chunk and the log
 // the words after them, so sparse spectra get wide super-chunks and dense
 // ones long logs.  A super-chunk whose planes and log do not fit is searched
@@ -39,7 +43,7 @@
 
 constexpr int kMaxHot = 6;                 // bitmap slices (b or y bitmap of a hot bucket) per spectrum
 constexpr int kMaxWarps = 16;              // CTAs of up to 512 threads
-constexpr int kTouchCap = 4096;            // touched list of a direct-counter column
+constexpr int kTouchCap = 3584;            // touched list of a direct-counter column (more: full scan)
 constexpr uint32_t kMaxCols = 12;          // widest super-chunk (columns of kChunk ids)
 constexpr uint32_t kSlots = 1024;          // candidate counters per round
 constexpr uint32_t kRound = 768;           // candidates per round (+31 at most)
@@ -50,7 +54,8 @@ constexpr uint32_t kRound = 768;           // candidates per round (+31 at most)
 // or [0, 16384) direct counters (over lists and slots, which are zero then)
 constexpr uint32_t kDynWords = kChunk + 1024;
 constexpr uint32_t kSlotWord = kDynWords - 2 * kSlots;
-constexpr uint32_t kListWord = kSlotWord - kSlots;
+constexpr uint32_t kListWords = 1152;       // compaction lists: up to 3 groups of 32 slots per warp
+constexpr uint32_t kListWord = kSlotWord - kListWords;
 constexpr uint32_t kMaxRounds = kListWord / kRound + 2;
 static_assert(2 * kMaxCols * kChunk / 32 < kListWord, "planes of the widest super-chunk leave room for a log");
 
@@ -85,58 +90,36 @@ struct SearchArgs {
     unsigned long long* work;   // unit counter
 };
 
+__device__ __forceinline__ bool better(int64_t ka, uint32_t pa, int64_t kb, uint32_t pb) {
+    return ka > kb || (ka == kb && pa < pb);
+}
+
+// A warp's best k candidates of the current unit, sorted by (key desc, pid
+// asc), in shared memory; one lane at a time inserts (warp-synchronous).
 template <int KMAX>
-struct TopK {
+struct WarpTop {
     int64_t key[KMAX];
     uint32_t pid[KMAX];
     uint32_t pk[KMAX];
     int n;
-    int64_t tkey;     // the k-th entry while the list is full
-    uint32_t tpid;
-    __device__ __forceinline__ void init() {
-        n = 0;
-        tkey = INT64_MIN;
-        tpid = 0xffffffffu;
-#pragma unroll
-        for (int i = 0; i < KMAX; ++i) { key[i] = INT64_MIN; pid[i] = 0xffffffffu; pk[i] = 0; }
+    __device__ __forceinline__ bool passes(int64_t kk, uint32_t p, int k) const {
+        return n < k || better(kk, p, key[k - 1], pid[k - 1]);
     }
-    // sorted by (key desc, pid asc); keeps the best k
     __device__ __forceinline__ void insert(int64_t kk, uint32_t p, uint32_t packed, int k) {
-        if (n == k && !(kk > tkey || (kk == tkey && p < tpid))) return;   // not among the best k
-        int pos = 0;
-#pragma unroll
-        for (int i = 0; i < KMAX; ++i)
-            if (i < n && (key[i] > kk || (key[i] == kk && pid[i] < p))) pos = i + 1;
-        if (pos >= k) return;
-#pragma unroll
-        for (int i = KMAX - 1; i > 0; --i)
-            if (i > pos) { key[i] = key[i - 1]; pid[i] = pid[i - 1]; pk[i] = pk[i - 1]; }
-#pragma unroll
-        for (int i = 0; i < KMAX; ++i)
-            if (i == pos) { key[i] = kk; pid[i] = p; pk[i] = packed; }
-        if (n < k) ++n;
-        if (n == k) {   // the worst of the first k
-            int64_t tk = INT64_MAX;
-            uint32_t tp = 0u;
-#pragma unroll
-            for (int i = 0; i < KMAX; ++i)
-                if (i < k && (key[i] < tk || (key[i] == tk && pid[i] > tp))) { tk = key[i]; tp = pid[i]; }
-            tkey = tk;
-            tpid = tp;
+        if (!passes(kk, p, k)) return;
+        int pos = n < k ? n : k - 1;
+        while (pos > 0 && better(kk, p, key[pos - 1], pid[pos - 1])) {
+            key[pos] = key[pos - 1];
+            pid[pos] = pid[pos - 1];
+            pk[pos] = pk[pos - 1];
+            --pos;
         }
-    }
-    __device__ __forceinline__ void pop() {
-#pragma unroll
-        for (int i = 0; i < KMAX - 1; ++i) { key[i] = key[i + 1]; pid[i] = pid[i + 1]; pk[i] = pk[i + 1]; }
-        key[KMAX - 1] = INT64_MIN;
-        pid[KMAX - 1] = 0xffffffffu;
-        --n;
+        key[pos] = kk;
+        pid[pos] = p;
+        pk[pos] = packed;
+        if (n < k) ++n;
     }
 };
-
-__device__ __forceinline__ bool better(int64_t ka, uint32_t pa, int64_t kb, uint32_t pb) {
-    return ka > kb || (ka == kb && pa < pb);
-}
 
 struct SearchShared {
     uint64_t pbase[kMaxTopN];         // bucket start of each ordinary peak
@@ -157,9 +140,6 @@ struct SearchShared {
     uint32_t slice_inc[kMaxHot];      // counter increment of a set bit
     uint32_t hist[kHistBins];
     int64_t lf[kMaxLen + 1];
-    int64_t wkey[kMaxWarps];
-    uint32_t wpid[kMaxWarps];
-    uint32_t wpk[kMaxWarps];
     uint32_t wsum[kMaxWarps];
     uint32_t wcand[kMaxWarps];
     int nnorm, nhotc, nslices, nhotpeaks;
@@ -235,7 +215,7 @@ __device__ __forceinline__ void scan_runs_2(SearchShared& sh, int buf, int nnorm
 }
 
 template <int KMAX, int THREADS>
-__global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel(SearchArgs a) {
+__global__ void __launch_bounds__(THREADS, THREADS <= 384 ? 2 : 1) search_kernel(SearchArgs a) {
     extern __shared__ __align__(16) uint32_t smem32[];   // kDynWords words (layout above)
     uint32_t* const cnt = smem32;
     uint32_t* const seen = smem32;
@@ -243,7 +223,10 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel
     unsigned long long* const tab = reinterpret_cast<unsigned long long*>(smem32 + kSlotWord);
     __shared__ SearchShared sh;
     constexpr int nwarps = THREADS / 32;
-    constexpr int PPT = kMaxTopN / THREADS;             // ordinary peaks per thread (at most)
+    constexpr int PPT = (kMaxTopN + THREADS - 1) / THREADS;   // ordinary peaks per thread (at most)
+    constexpr int kListStride = (32 / nwarps + (32 % nwarps ? 1 : 0)) * 32;   // list words per warp
+    static_assert(kListStride * nwarps <= (int)kListWords, "compaction lists fit");
+    __shared__ WarpTop<KMAX> wtop[nwarps];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const uint32_t last_col = a.skip_stride - 1;
@@ -251,6 +234,7 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel
     for (int i = tid; i < (int)kHistBins; i += THREADS) sh.hist[i] = 0;
     for (int i = tid; i <= (int)kMaxLen; i += THREADS) sh.lf[i] = a.lf[i];
     if (tid == 0) { sh.ncand[0] = 0u; sh.ncand[1] = 0u; }
+    if (tid < nwarps) wtop[tid].n = 0;
     const uint64_t total_units = a.seg_off[a.n];
     const int k = (int)a.k;
     const uint32_t min_shared = a.min_shared;
@@ -376,8 +360,10 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel
             }
             __syncthreads();   // wsum is reused by the scans
         }
-        TopK<KMAX> top;
-        top.init();
+        // a lane's scored candidate waiting for its warp's list (flush)
+        int64_t pK = 0;
+        uint32_t pP = 0u, pC = 0u;
+        bool pend = false;
         uint32_t* twice = smem32;   // the current super-chunk's twice plane and log
         uint32_t* logw = smem32;
 
@@ -426,8 +412,20 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel
                 const int64_t K = sh.lf[nb] + sh.lf[ny] + __ldg(a.ls + S);
                 const int64_t hb = K >> 31;
                 atomicAdd(&sh.hist[hb > 255 ? 255 : (hb < 0 ? 0 : hb)], 1u);
-                top.insert(K, pid, c, k);
+                if (wtop[warp].passes(K, pid, k)) { pK = K; pP = pid; pC = c; pend = true; }
             }
+        };
+        // pending candidates into the warp's list, one lane at a time; every
+        // lane of the warp calls it (convergent points only)
+        auto flush = [&]() {
+            unsigned pm = __ballot_sync(0xffffffffu, pend);
+            while (pm) {
+                const int l = __ffs(pm) - 1;
+                pm &= pm - 1;
+                if (lane == l) wtop[warp].insert(pK, pP, pC, k);
+                __syncwarp();
+            }
+            pend = false;
         };
         // one counter (c, pid): filter, add the hot slices, score
         auto visit = [&](uint32_t c, uint32_t pid) {
@@ -457,26 +455,30 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel
             __syncthreads();
             const int nt = sh.ntouched;
             if (nt <= kTouchCap && !hot_alone) {
-                for (int i = tid; i < nt; i += THREADS) {
-                    const uint32_t w = sh.touched[i];
-                    const uint32_t c = cnt[w];
-                    cnt[w] = 0u;
-                    visit(c, cb + w);
+                for (int i0 = warp * 32; i0 < nt; i0 += THREADS) {   // warp-uniform trip count
+                    const int i = i0 + lane;
+                    if (i < nt) {
+                        const uint32_t w = sh.touched[i];
+                        const uint32_t c = cnt[w];
+                        cnt[w] = 0u;
+                        visit(c, cb + w);
+                    }
+                    flush();
                 }
             } else {
                 // every counter, 32 peptide ids per step; bitmaps alone can
                 // qualify a peptide when hot_alone
-                for (uint32_t gi = tid; gi < kChunk / 32; gi += THREADS) {
+                for (uint32_t gi = tid; gi < kChunk / 32; gi += THREADS) {   // warp-uniform trip count
                     const uint32_t gp = cb + (gi << 5);
-                    if (gp + 32 <= x0 || gp >= x1) continue;
+                    const bool act = !(gp + 32 <= x0 || gp >= x1);
                     const uint32_t lo_b = x0 > gp ? x0 - gp : 0u;
                     const uint32_t hi_b = x1 - gp >= 32u ? 32u : x1 - gp;
                     const uint32_t valid = (hi_b >= 32u ? 0xffffffffu : ((1u << hi_b) - 1u)) & ~((1u << lo_b) - 1u);
                     uint32_t hw[kMaxHot];
 #pragma unroll
-                    for (int s = 0; s < kMaxHot; ++s) hw[s] = s < nslices ? __ldg(sh.slice[s] + (gp >> 5)) : 0u;
+                    for (int s = 0; s < kMaxHot; ++s) hw[s] = act && s < nslices ? __ldg(sh.slice[s] + (gp >> 5)) : 0u;
                     uint32_t cand = 0;
-                    for (int j = 0; j < 32; ++j) {
+                    for (int j = 0; act && j < 32; ++j) {
                         const int jb = (j + lane) & 31;   // rotated: lanes hit different banks
                         const uint32_t c = cnt[(gi << 5) + jb];
                         uint32_t hc = 0;
@@ -485,18 +487,23 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel
                         const uint32_t nn = (c >> kNbShift) + ((c >> kNyShift) & 63u);
                         if ((c != 0u || hc > 0u) && nn + hc >= min_shared) cand |= 1u << jb;
                     }
-                    cand &= valid;
-                    while (cand) {
-                        const int jb = __ffs(cand) - 1;
-                        cand &= cand - 1;
-                        uint32_t c = cnt[(gi << 5) + jb];
+                    cand &= act ? valid : 0u;
+                    while (__any_sync(0xffffffffu, cand != 0u)) {   // one candidate a lane per step
+                        if (cand) {
+                            const int jb = __ffs(cand) - 1;
+                            cand &= cand - 1;
+                            uint32_t c = cnt[(gi << 5) + jb];
 #pragma unroll
-                        for (int s = 0; s < kMaxHot; ++s)
-                            if ((hw[s] >> jb) & 1u) c += sh.slice_inc[s];
-                        score(c, gp + jb);
+                            for (int s = 0; s < kMaxHot; ++s)
+                                if ((hw[s] >> jb) & 1u) c += sh.slice_inc[s];
+                            score(c, gp + jb);
+                        }
+                        flush();
                     }
+                    if (act) {
 #pragma unroll 4
-                    for (int j = 0; j < 32; ++j) cnt[(gi << 5) + ((j + lane) & 31)] = 0u;
+                        for (int j = 0; j < 32; ++j) cnt[(gi << 5) + ((j + lane) & 31)] = 0u;
+                    }
                 }
             }
             __syncthreads();
@@ -567,8 +574,9 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel
         // plane.  Warp w owns words [w * wpw, (w + 1) * wpw), lane l every
         // 32nd of them (barriers inside).
         auto mark = [&](uint32_t cb, uint32_t words) {
-            const uint32_t wpw = words / nwarps;   // a multiple of 32
-            const uint32_t wbeg = (uint32_t)warp * wpw;
+            const uint32_t G = words >> 5;          // groups of 32 plane words, split evenly over the warps
+            const uint32_t g0 = (uint32_t)warp * G / nwarps, g1 = (uint32_t)(warp + 1) * G / nwarps;
+            const uint32_t wbeg = g0 << 5, wpw = (g1 - g0) << 5;
             uint32_t mine = 0;
             for (uint32_t i = lane; i < wpw; i += 32) {
                 const uint32_t w = wbeg + i;
@@ -664,27 +672,28 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel
         // indices of its share [w * spw, (w + 1) * spw) into its list words,
         // visits them with all lanes, and zeroes the slots and the list.
         auto slots_epilogue = [&](uint32_t cb) {
-            constexpr uint32_t spw = kSlots / nwarps;
-            const uint32_t base = (uint32_t)warp * spw;
+            const uint32_t base = (uint32_t)warp * kListStride;
             uint32_t cnt = 0;
-#pragma unroll
-            for (uint32_t i0 = 0; i0 < spw; i0 += 32) {
-                const uint32_t sl = base + i0 + lane;
+            for (uint32_t g = warp; g < kSlots / 32; g += nwarps) {   // groups of 32 slots
+                const uint32_t sl = (g << 5) + lane;
                 const bool occ = tab[sl] != 0ull;
                 const unsigned msk = __ballot_sync(0xffffffffu, occ);
                 if (occ) lists[base + cnt + __popc(msk & lt)] = sl;
                 cnt += __popc(msk);
             }
             __syncwarp();
-            for (uint32_t i = lane; i < cnt; i += 32) {
-                const uint32_t sl = lists[base + i];
-                const unsigned long long v = tab[sl];
-                tab[sl] = 0ull;
-                visit((uint32_t)v, cb + (uint32_t)(v >> 32));
+            for (uint32_t i0 = 0; i0 < cnt; i0 += 32) {
+                const uint32_t i = i0 + lane;
+                if (i < cnt) {
+                    const uint32_t sl = lists[base + i];
+                    const unsigned long long v = tab[sl];
+                    tab[sl] = 0ull;
+                    visit((uint32_t)v, cb + (uint32_t)(v >> 32));
+                }
+                flush();
             }
             __syncwarp();
-#pragma unroll
-            for (uint32_t i0 = 0; i0 < spw; i0 += 32) lists[base + i0 + lane] = 0u;
+            for (uint32_t i0 = 0; i0 < (uint32_t)kListStride; i0 += 32) lists[base + i0 + lane] = 0u;
         };
         // zeroes plane words [w0, w1), both multiples of 4
         auto clear_words = [&](uint32_t* plane, uint32_t w0, uint32_t w1) {
@@ -804,32 +813,35 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 256 ? 2 : 1) search_kernel
             e = ne;
             __syncthreads();
         }
-        // block top-k: k rounds of block-wide argmax over the thread heads
-        for (int r = 0; r < k; ++r) {
-            int64_t bk = top.n > 0 ? top.key[0] : INT64_MIN;
-            uint32_t bp = top.n > 0 ? top.pid[0] : 0xffffffffu;
-            uint32_t bpk = top.n > 0 ? top.pk[0] : 0u;
+        // the unit's top-k: thread 0 merges the warps' lists
+        __syncthreads();
+        if (tid == 0) {
+            int hd[nwarps];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const int64_t ok = __shfl_xor_sync(0xffffffffu, bk, o);
-                const uint32_t op = __shfl_xor_sync(0xffffffffu, bp, o);
-                const uint32_t opk = __shfl_xor_sync(0xffffffffu, bpk, o);
-                if (better(ok, op, bk, bp)) { bk = ok; bp = op; bpk = opk; }
-            }
-            if (lane == 0) { sh.wkey[warp] = bk; sh.wpid[warp] = bp; sh.wpk[warp] = bpk; }
-            __syncthreads();
-            bk = sh.wkey[0]; bp = sh.wpid[0]; bpk = sh.wpk[0];
-            for (int w = 1; w < nwarps; ++w)
-                if (better(sh.wkey[w], sh.wpid[w], bk, bp)) { bk = sh.wkey[w]; bp = sh.wpid[w]; bpk = sh.wpk[w]; }
-            if (top.n > 0 && top.pid[0] == bp && top.key[0] == bk && bp != 0xffffffffu) top.pop();
-            if (tid == 0) {
+            for (int w = 0; w < nwarps; ++w) hd[w] = 0;
+            for (int r = 0; r < k; ++r) {
+                int bw = -1;
+                int64_t bk = INT64_MIN;
+                uint32_t bp = 0xffffffffu, bpk = 0u;
+#pragma unroll
+                for (int w = 0; w < nwarps; ++w) {
+                    if (hd[w] < wtop[w].n) {
+                        const int64_t kk = wtop[w].key[hd[w]];
+                        const uint32_t pp = wtop[w].pid[hd[w]];
+                        if (bw < 0 || better(kk, pp, bk, bp)) { bw = w; bk = kk; bp = pp; bpk = wtop[w].pk[hd[w]]; }
+                    }
+                }
+#pragma unroll
+                for (int w = 0; w < nwarps; ++w)
+                    if (w == bw) ++hd[w];
                 UnitTop o;
-                o.key = bk;
-                o.pid = bp;
-                o.packed = bpk;
+                o.key = bw >= 0 ? bk : INT64_MIN;
+                o.pid = bw >= 0 ? bp : 0xffffffffu;
+                o.packed = bw >= 0 ? bpk : 0u;
                 a.utop[u * k + r] = o;
             }
-            __syncthreads();
+#pragma unroll
+            for (int w = 0; w < nwarps; ++w) wtop[w].n = 0;
         }
         // histogram of this unit into the spectrum's histogram
         uint32_t mine = 0;
