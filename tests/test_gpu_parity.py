@@ -212,7 +212,14 @@ def test_parity_open_medium_full_index_sampled(gpu, oracle_lib):
     w = configs.OPEN_MEDIUM
     prot, idx, db = build_both(oracle_lib, w)
     spec = synth.make_spectra(prot, w)
-    got = idx.search(spec)
+    got = idx.search(spec)          # through host buffers
+    dev = hc.DeviceResult.alloc(spec.n, w.params.top_k)
+    idx.search_device(hc.DeviceBatch.from_spectra(spec), dev)   # device buffers, same launch
+    gpu.cuda.synchronize()
+    whole = dev.to_host(spec.n, w.params.top_k)
+    np.testing.assert_array_equal(got.psm, whole.psm)
+    np.testing.assert_array_equal(got.hist, whole.hist)
+    np.testing.assert_array_equal(got.n_scored, whole.n_scored)
     sel = np.array([0, 1, 12345, 54321, 99999], dtype=np.uint32)
     ref = db.search(spec, sel=sel)
     assert_parity(got, ref, sel=sel, label="open_medium")
