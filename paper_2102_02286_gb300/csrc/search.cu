@@ -98,13 +98,14 @@ hicops_status alloc_workspace(A& al, const hicops_params& p, uint32_t cap_n, uin
     return HICOPS_OK;
 }
 
-int g_sm_count = 0;
+std::atomic<int> g_sm_count{0};   // set on first use; every thread computes the same value
 
 hicops_status sm_count() {
-    if (!g_sm_count) {
-        int dev;
+    if (!g_sm_count.load(std::memory_order_relaxed)) {
+        int dev, c = 0;
         HC_CUDA(cudaGetDevice(&dev));
-        HC_CUDA(cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev));
+        HC_CUDA(cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev));
+        g_sm_count.store(c, std::memory_order_relaxed);
     }
     return HICOPS_OK;
 }
@@ -119,9 +120,11 @@ hicops_status check_config(const hicops_search_config& c) {
     return HICOPS_OK;
 }
 
-hicops_search_config resolved(const hicops_search_config& c) {
+// Default shape: 384-thread CTAs (two fit an SM while the top-k lists are
+// at most 16 long), else 256.
+hicops_search_config resolved(const hicops_search_config& c, uint32_t k) {
     hicops_search_config r = c;
-    if (!r.threads) r.threads = 256;
+    if (!r.threads) r.threads = k <= 16 ? 384 : 256;
     if (!r.chunk_entries) r.chunk_entries = 2;
     return r;
 }
@@ -129,7 +132,7 @@ hicops_search_config resolved(const hicops_search_config& c) {
 // Units per spectrum cap: large when the batch cannot fill the GPU.
 uint32_t max_segments(const hicops_search_config& c, uint32_t n) {
     if (c.seg_pids) return kMaxSegs;
-    const uint32_t want = 8u * (uint32_t)g_sm_count;
+    const uint32_t want = 8u * (uint32_t)g_sm_count.load(std::memory_order_relaxed);
     uint32_t m = (want + n - 1) / (n ? n : 1);
     if (m < 1) m = 1;
     if (m > (uint32_t)kMaxSegs) m = kMaxSegs;
@@ -138,19 +141,19 @@ uint32_t max_segments(const hicops_search_config& c, uint32_t n) {
 
 template <int KMAX, int THREADS>
 hicops_status launch_search_t(const SearchArgs& sa, uint32_t ctas_per_sm, uint64_t max_units, cudaStream_t s) {
-    static int occ = -1;
+    static std::atomic<int> occ{-1};   // CTAs per SM; concurrent first calls compute the same value
     const size_t smem = sizeof(uint32_t) * kDynWords;   // 68 KB: the kernel's planes, log, slots / counters
-    if (occ < 0) {
+    if (occ.load(std::memory_order_acquire) < 0) {
         HC_CUDA(cudaFuncSetAttribute(search_kernel<KMAX, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
         int b = 0;
         HC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, search_kernel<KMAX, THREADS>, THREADS, smem));
-        occ = b < 1 ? 1 : b;
+        occ.store(b < 1 ? 1 : b, std::memory_order_release);
     }
-    int per_sm = occ;
+    int per_sm = occ.load(std::memory_order_acquire);
     if (ctas_per_sm && (int)ctas_per_sm < per_sm) per_sm = (int)ctas_per_sm;
     // no more CTAs than work units can exist
-    uint64_t grid = (uint64_t)g_sm_count * per_sm;
+    uint64_t grid = (uint64_t)g_sm_count.load(std::memory_order_relaxed) * per_sm;
     if (max_units < grid) grid = max_units ? max_units : 1;
     search_kernel<KMAX, THREADS><<<(unsigned)grid, THREADS, smem, s>>>(sa);
     count_launches(1);
@@ -183,7 +186,7 @@ hicops_status enqueue_search(hicops_index* idx, const DevBatch& d, uint32_t n, c
                              cudaStream_t s, bool timing_marks) {
     const hicops_params& p = idx->p;
     const DeviceIndex& di = idx->dev;
-    const hicops_search_config cfg = resolved(cfg_in);
+    const hicops_search_config cfg = resolved(cfg_in, idx->p.top_k);
     const uint32_t k = p.top_k;
     mark(idx, 0, s, timing_marks);
     PrepArgs pa{d.peak_off, d.mz, d.inten, d.prec, d.z, d.tol, n, p.top_n_peaks, p.bin_width_da, p.frag_mz_min,

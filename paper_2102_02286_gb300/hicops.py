@@ -258,14 +258,18 @@ class Index:
         b = Batch(len(arrs[3]), 0, *[_ptr(a).value for a in arrs], None)
         return b, arrs
 
-    def search(self, spec) -> SearchResult:
+    def search(self, spec, out: Optional[SearchResult] = None) -> SearchResult:
+        """Search through host buffers.  `out` may hold preallocated result
+        arrays (e.g. views of page-locked memory) of the batch's size."""
         b, keep = self._host_batch(spec)
         n = b.n
-        psm = np.zeros((n, self.top_k), PSM_DTYPE)
-        hist = np.zeros((n, HIST_BINS), np.uint32)
-        ns = np.zeros(n, np.uint32)
-        _check(load().hicops_search(self.h, C.byref(b), _ptr(psm), _ptr(hist), _ptr(ns)))
-        return SearchResult(psm, hist, ns)
+        if out is None:
+            out = SearchResult(np.zeros((n, self.top_k), PSM_DTYPE), np.zeros((n, HIST_BINS), np.uint32),
+                               np.zeros(n, np.uint32))
+        if out.psm.shape != (n, self.top_k) or out.hist.shape != (n, HIST_BINS) or out.n_scored.shape != (n,):
+            raise ValueError("out arrays do not match the batch")
+        _check(load().hicops_search(self.h, C.byref(b), _ptr(out.psm), _ptr(out.hist), _ptr(out.n_scored)))
+        return out
 
     def search_work(self, spec):
         """Per spectrum: window [lo, hi), retained peaks, index entries in the window (H)."""
