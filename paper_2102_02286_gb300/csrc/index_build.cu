@@ -388,8 +388,8 @@ hicops_status upload_index(hicops_index* idx) {
             std::swap(keys, keys2);
         }
     }
-    // 4 spare words: the search's L2 prefetch of a run rounds its end up to 16 bytes
-    HC_CUDA(cudaMalloc(&d.entry, sizeof(uint32_t) * (E + 4)));
+    // one spare word: the allocation is never empty
+    HC_CUDA(cudaMalloc(&d.entry, sizeof(uint32_t) * (E + 1)));
     if (E) take_low_kernel<<<(unsigned)((E + 255) / 256), 256, 0, s>>>(keys, E, d.entry);
     bucket_off_kernel<<<(unsigned)((E + 1 + 255) / 256), 256, 0, s>>>(keys, E, idx->n_bins, d.off);
     HC_CUDA(cudaGetLastError());

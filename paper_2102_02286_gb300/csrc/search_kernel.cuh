@@ -700,21 +700,6 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 384 ? 2 : 1) search_kernel
             uint4* p4 = reinterpret_cast<uint4*>(plane);
             for (uint32_t i = w0 / 4 + tid; i < w1 / 4; i += THREADS) p4[i] = make_uint4(0u, 0u, 0u, 0u);
         };
-        // L2 prefetch of this thread's runs [ra, rb) (the next super-chunk's)
-        auto prefetch_runs = [&]() {
-#pragma unroll
-            for (int i = 0; i < PPT; ++i) {
-                const int t = tid * ppt + i;
-                if (i < ppt && t < nnorm && rb[i] > ra[i]) {
-                    const uint32_t* p0 = a.entry + sh.pbase[t] + ra[i];
-                    const uint64_t s0 = reinterpret_cast<uint64_t>(p0) & ~uint64_t(15);
-                    const uint64_t s1 = (reinterpret_cast<uint64_t>(p0 + (rb[i] - ra[i])) + 15) & ~uint64_t(15);
-                    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(s0), "r"((uint32_t)(s1 - s0))
-                                 : "memory");
-                }
-            }
-        };
-
         // prologue: bounds of the first super-chunk
         uint32_t c = col_lo;
         uint32_t e = min(col_lo + m, col_end);
@@ -776,10 +761,7 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 384 ? 2 : 1) search_kernel
             if (more) load_runs(nc, ne);                 // next super-chunk's bounds: in flight during pass A
             pass_a(buf, cbase, x0, x1, par);
             uint32_t excl = 0;
-            if (more) {                                   // its runs into L2 while this one finishes
-                prefetch_runs();
-                excl = scan_runs_1<PPT>(sh, nnorm, ppt, ra, rb);
-            }
+            if (more) excl = scan_runs_1<PPT>(sh, nnorm, ppt, ra, rb);
             if (2 * words < log_lo) log_lo = 2 * words;
             if (2 * words + R > log_dirty) log_dirty = 2 * words + R;
             __syncthreads();
