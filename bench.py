@@ -18,6 +18,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -167,7 +168,8 @@ def cpu_baseline(w, prot, spec, n_sample: int):
     t0 = time.perf_counter()
     db.search(spec, sel=sel)
     dt = time.perf_counter() - t0
-    return {"value": len(sel) / dt, "unit": "spectra/s", "cores": 1, "kind": "oracle",
+    return {"value": len(sel) / dt, "unit": "spectra/s", "cores": 1, "host_cores": os.cpu_count(),
+            "host_arch": platform.machine(), "kind": "oracle",
             "sample": f"{len(sel)} spectra of {w.name} (same index and spectra as the timed run), "
                       f"single-threaded FP64 all-pairs oracle, {dt:.1f} s"}
 
@@ -198,7 +200,8 @@ def run_reference(args):
             "ms_per_step": 1000 * total / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_desc(w), "spectra_per_step": per_step},
-            "cpu_baseline": {"value": value, "unit": "spectra/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": "spectra/s", "cores": 1, "host_cores": os.cpu_count(),
+                             "host_arch": platform.machine(), "kind": "oracle",
                              "sample": f"{per_step} spectra per step of {w.name}"},
             "e2e": {"value": value, "unit": "spectra/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -592,8 +595,20 @@ def main():
     achieved = search_bytes / mean_search_s / 1e9
     rec = search_traffic_record()
     traffic = None
+    atomics = None
     if rec is not None and rec["workload"] == w.name:
         traffic = float(rec["dram_bytes_per_spectrum"]) * n
+        wf = rec.get("shared_atomic_wavefronts_per_spectrum")
+        if wf is not None:
+            # the secondary ceiling: one shared-memory wavefront per SM per clock
+            sms = torch.cuda.get_device_properties(0).multi_processor_count
+            mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz")
+            a_rate = float(wf) * n / mean_search_s
+            a_peak = sms * mhz * 1e6 if mhz else None
+            atomics = {"achieved": a_rate, "peak": a_peak, "unit": "shared-atomic wavefronts/s",
+                       "frac": a_rate / a_peak if a_peak else None,
+                       "per_spectrum": float(wf), "source": "ncu capture in profiles/search_kernel_traffic.json",
+                       "peak_basis": f"{sms} SMs x {mhz} MHz x 1 wavefront per SM-clock"}
     line = {
         "metric": STEP_METRIC,
         "value": value,
@@ -637,6 +652,8 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    if atomics is not None:
+        line["shared_atomics"] = atomics
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, prot, spec, args.oracle_spectra)
     idx.close()
