@@ -41,7 +41,8 @@ class OrParams(C.Structure):
                 ("pad0", C.c_uint32), ("min_mass", C.c_double), ("max_mass", C.c_double),
                 ("frag_mz_min", C.c_double), ("frag_mz_max", C.c_double), ("bin_width", C.c_double),
                 ("top_n_peaks", C.c_uint32), ("min_shared", C.c_uint32), ("top_k", C.c_uint32),
-                ("hist_bins", C.c_uint32), ("intensity_scale", C.c_uint32), ("max_total_mods", C.c_uint32)]
+                ("hist_bins", C.c_uint32), ("intensity_scale", C.c_uint32), ("max_total_mods", C.c_uint32),
+                ("tol_bins", C.c_uint32), ("pad1", C.c_uint32)]
 
 
 PSM_DTYPE = np.dtype([("pid", np.uint32), ("nb", np.uint32), ("ny", np.uint32), ("S", np.uint32),
@@ -91,7 +92,8 @@ def make_params(sp) -> OrParams:
                     min_mass=sp.min_mass, max_mass=sp.max_mass, frag_mz_min=sp.frag_mz_min,
                     frag_mz_max=sp.frag_mz_max, bin_width=sp.bin_width_da, top_n_peaks=sp.top_n_peaks,
                     min_shared=sp.min_shared, top_k=sp.top_k, hist_bins=sp.hist_bins,
-                    intensity_scale=sp.intensity_scale, max_total_mods=sp.max_total_mods)
+                    intensity_scale=sp.intensity_scale, max_total_mods=sp.max_total_mods,
+                    tol_bins=sp.tol_bins, pad1=0)
 
 
 @dataclass

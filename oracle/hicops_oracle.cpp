@@ -33,6 +33,11 @@
 //      b_i = sum_{j<=i} m_j + proton;  y_i = (sum_{j=L..i+1} m_j + H2O) + proton;
 //   R6 bin(mz) = floor(mz / w) for frag_mz_min <= mz < frag_mz_max; a peak
 //      and an ion are shared iff their bins are equal (w = dF);
+//   R15 (fragment tolerance of t bins, dF = t * w on a finer grid) an ion
+//      bin x is shared iff some retained peak bin b has |x - b| <= t, i.e.
+//      x lies in the union of the peaks' windows [b - t, b + t]; it counts
+//      once and contributes the largest iq of the peaks covering it; t = 0
+//      is R6;
 //   R7 a peptide's ion set is its set of distinct bins; a bin holding both a
 //      b and a y ion of the same peptide counts once, as b;
 //   R8 preprocessing: drop non-finite / non-positive / out-of-range peaks,
@@ -100,6 +105,7 @@ struct OrParams {
     double frag_mz_min, frag_mz_max, bin_width;
     uint32_t top_n_peaks, min_shared, top_k, hist_bins;
     uint32_t intensity_scale, max_total_mods;
+    uint32_t tol_bins, pad1;   // R15 fragment tolerance in bins (0 = R6)
 };
 
 // One PSM row of the oracle's output.
@@ -249,6 +255,20 @@ Query preprocess(const OrParams& p, const float* mz, const float* inten, uint64_
         q.iq.push_back(iq);
     }
     return q;
+}
+
+// R15: is ion bin x inside some retained peak's window [b - t, b + t]?  If
+// so, iq = the largest quantised intensity of the peaks whose window holds x.
+bool covered(const Query& q, uint32_t x, uint32_t t, uint32_t& iq) {
+    const uint32_t from = x > t ? x - t : 0u;
+    auto it = std::lower_bound(q.bins.begin(), q.bins.end(), from);   // first peak with b >= x - t
+    bool hit = false;
+    iq = 0;
+    for (; it != q.bins.end() && (uint64_t)*it <= (uint64_t)x + t; ++it) {
+        hit = true;
+        iq = std::max(iq, q.iq[it - q.bins.begin()]);
+    }
+    return hit;
 }
 
 double log10_factorial(uint32_t n) {
@@ -443,10 +463,16 @@ void or_search_shard(void* h, const uint64_t* peak_off, const float* mz, const f
                 auto ib = ion_bins(*db, db->peps[pid]);
                 uint32_t nb = 0, ny = 0, S = 0;
                 for (auto& bt : ib) {
-                    auto it = std::lower_bound(q.bins.begin(), q.bins.end(), bt.first);
-                    if (it == q.bins.end() || *it != bt.first) continue;
+                    uint32_t iq = 0;
+                    if (p.tol_bins == 0) {   // R6: equal bins
+                        auto it = std::lower_bound(q.bins.begin(), q.bins.end(), bt.first);
+                        if (it == q.bins.end() || *it != bt.first) continue;
+                        iq = q.iq[it - q.bins.begin()];
+                    } else if (!covered(q, bt.first, p.tol_bins, iq)) {   // R15
+                        continue;
+                    }
                     if (bt.second) ny++; else nb++;
-                    S += q.iq[it - q.bins.begin()];
+                    S += iq;
                 }
                 if (nb + ny < p.min_shared) continue;
                 OrPsm c;

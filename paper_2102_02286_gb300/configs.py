@@ -46,6 +46,9 @@ class SearchParams:
     frag_mz_min: float = 100.0
     frag_mz_max: float = 2000.0
     bin_width_da: float = 0.01
+    # fragment tolerance in bins on that grid (dF = tol_bins * bin_width_da):
+    # a peak in bin b covers bins b - tol_bins .. b + tol_bins; 0 = equal bins
+    tol_bins: int = 0
     # scoring
     top_n_peaks: int = 100
     min_shared: int = 4

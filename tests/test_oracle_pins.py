@@ -12,8 +12,13 @@
 * a brute-force re-implementation on tiny inputs (different digestion,
   enumeration, ordering and all-pairs matching code);
 * invariants: shared counts <= min(query bins, peptide bins), window
-  monotonicity, and the self-match of a noise-free spectrum.
+  monotonicity, and the self-match of a noise-free spectrum;
+* the fragment tolerance of t bins (R15): a hand-worked spectrum with peaks
+  one and two bins off the ions and two peaks covering one ion, the brute
+  force above with every (ion, peak) pair compared by bin distance, the
+  closed form when every peak covers every bin, and monotonicity in t.
 """
+import dataclasses
 import itertools
 import math
 import os
@@ -64,9 +69,9 @@ def paper_peptides():
         return [l.strip() for l in f if l.strip() and not l.startswith("#")]
 
 
-def single_peptide_db(oracle_lib, seq, mods=(configs.CARBAMIDOMETHYL_C,)):
+def single_peptide_db(oracle_lib, seq, mods=(configs.CARBAMIDOMETHYL_C,), **extra):
     """Database whose only protein is ``seq``; returns (db, pid of full seq)."""
-    p = SearchParams(min_len=2, max_len=60, missed_cleavages=10, min_mass=0.0, max_mass=1e5)
+    p = SearchParams(min_len=2, max_len=60, missed_cleavages=10, min_mass=0.0, max_mass=1e5, **extra)
     prot = np.frombuffer(seq.encode(), np.uint8)
     db = oracle_lib.OracleDb(prot, np.array([0, len(seq)], np.uint64), list(mods), p)
     hits = [i for i in range(db.n) if db.peptide(i)[0] == seq and not db.peptide(i)[2].any()]
@@ -383,13 +388,25 @@ def brute_force_search(prot_seqs, mods, p: SearchParams, spec):
                     yset.add(math.floor(ym / w))
             yset -= bset
             nb = ny = S = 0
-            for bn, iqv in qb.items():
-                if bn in bset:
-                    nb += 1
-                    S += iqv
-                elif bn in yset:
-                    ny += 1
-                    S += iqv
+            if p.tol_bins == 0:
+                for bn, iqv in qb.items():
+                    if bn in bset:
+                        nb += 1
+                        S += iqv
+                    elif bn in yset:
+                        ny += 1
+                        S += iqv
+            else:
+                # every (ion bin, peak bin) pair; an ion bin counts once, with
+                # the largest iq of the peaks within tol_bins of it
+                for x in bset | yset:
+                    cover = [iqv for bn, iqv in qb.items() if abs(bn - x) <= p.tol_bins]
+                    if cover:
+                        if x in bset:
+                            nb += 1
+                        else:
+                            ny += 1
+                        S += max(cover)
             if nb + ny >= p.min_shared:
                 lfb = lfy = 0.0
                 for i in range(2, nb + 1):
@@ -408,8 +425,20 @@ def brute_force_search(prot_seqs, mods, p: SearchParams, spec):
 
 @pytest.mark.parametrize("min_shared,tol", [(4, 500.0), (3, 50.0)])
 def test_oracle_matches_brute_force(oracle_lib, min_shared, tol):
+    check_against_brute_force(oracle_lib, SearchParams(missed_cleavages=1, min_shared=min_shared, top_k=5,
+                                                       top_n_peaks=60), tol)
+
+
+@pytest.mark.parametrize("tol_bins,min_shared", [(1, 4), (2, 3), (3, 4)])
+def test_tolerance_matches_brute_force(oracle_lib, tol_bins, min_shared):
+    # a 0.005 Da grid: dF = tol_bins * 0.005 Da
+    check_against_brute_force(oracle_lib, SearchParams(missed_cleavages=1, min_shared=min_shared, top_k=5,
+                                                       top_n_peaks=60, bin_width_da=0.005,
+                                                       tol_bins=tol_bins), 500.0)
+
+
+def check_against_brute_force(oracle_lib, params, tol):
     w = configs.OPEN_MEDIUM
-    params = SearchParams(missed_cleavages=1, min_shared=min_shared, top_k=5, top_n_peaks=60)
     prot = synth.make_proteome(12, seed=7, length=(60, 120))
     wl = configs.Workload("bf", 99, 12, w.mods, params,
                           configs.SpectraRecipe(n_spectra=12, noise_lo=30, noise_hi=60, tol_da=(tol,)))
@@ -508,3 +537,74 @@ def test_self_match_is_top1(oracle_lib, tiny):
             assert row and row[0]["key"] == top["key"]
         else:
             assert top["nb"] + top["ny"] == nb
+
+
+# ---------------------------------------------------------------- R15: t bins
+
+
+def test_tolerance_hand_case(oracle_lib):
+    scale = 10000
+    db, pid = single_peptide_db(oracle_lib, "SAMPLERTIDEK", tol_bins=0, min_shared=1, intensity_scale=scale)
+    bins, is_y = db.bins(pid)
+    bins = [int(b) for b in bins]
+    bb = [b for b, y in zip(bins, is_y) if not y]
+    yb = [b for b, y in zip(bins, is_y) if y]
+    xb1, xb2, yb1, yb2 = bb[1], bb[3], yb[1], yb[3]
+    # peak bin, intensity (iq = floor(I * scale / 1000))
+    peaks = [(xb1 + 1, 1000.0),    # one bin above a b ion: iq 10000
+             (yb1 - 1, 500.0),     # both sides of a y ion: iq 5000 ...
+             (yb1 + 1, 250.0),     # ... and 2500 (the ion takes the larger)
+             (xb2, 100.0),         # on a b ion: iq 1000
+             (yb2 + 2, 800.0)]     # two bins above a y ion: iq 8000
+    for b, _ in peaks:   # no other ion bin within 3 bins of a peak
+        near = [x for x in bins if abs(x - b) <= 3]
+        assert len(near) == 1
+    w = 0.01
+    _, mass, _ = db.peptide(pid)
+    sp = synth.spectra_from_lists([([(b + 0.5) * w for b, _ in peaks], [I for _, I in peaks])],
+                                  [(mass + 2 * PROTON_CONST) / 2], [2], [0.001])
+    want = {0: (1, 0, 1000), 1: (2, 1, 10000 + 5000 + 1000), 2: (2, 2, 10000 + 5000 + 1000 + 8000),
+            3: (2, 2, 24000)}
+    for t, (nb, ny, S) in want.items():
+        dbt, pt = single_peptide_db(oracle_lib, "SAMPLERTIDEK", tol_bins=t, min_shared=1, intensity_scale=scale)
+        assert pt == pid
+        r = dbt.search(sp)
+        rows = [x for x in r.psm[0] if x["pid"] == pid]
+        assert rows, t
+        assert (int(rows[0]["nb"]), int(rows[0]["ny"]), int(rows[0]["S"])) == (nb, ny, S), t
+
+
+def test_tolerance_covering_everything(oracle_lib, tiny):
+    # every retained peak covers every bin: each in-range ion bin is shared,
+    # each with the top peak's iq = intensity_scale
+    w, prot, spec, _ = tiny
+    p = dataclasses.replace(w.params, tol_bins=10 ** 7)
+    db = oracle_lib.OracleDb(prot.seq, prot.off, w.mods, p)
+    r = db.search(spec)
+    n_real = 0
+    for q in range(spec.n):
+        want = sum(1 for pid in range(int(r.lo[q]), int(r.hi[q]))
+                   if len(db.bins(pid)[0]) >= p.min_shared)
+        assert r.n_scored[q] == want
+        for row in r.psm[q]:
+            if row["pid"] == 0xFFFFFFFF:
+                continue
+            n_real += 1
+            bins, is_y = db.bins(int(row["pid"]))
+            assert (row["nb"], row["ny"]) == (int(np.sum(is_y == 0)), int(np.sum(is_y == 1)))
+            assert row["S"] == len(bins) * p.intensity_scale
+    assert n_real > 0
+
+
+def test_tolerance_monotone(oracle_lib, tiny):
+    # a larger t covers a superset of bins, each with a larger-or-equal iq
+    w, prot, spec, _ = tiny
+    prev = None
+    for t in (0, 1, 2, 4):
+        db = oracle_lib.OracleDb(prot.seq, prot.off, w.mods, dataclasses.replace(w.params, tol_bins=t))
+        r = db.search(spec)
+        if prev is not None:
+            assert np.all(r.n_scored >= prev.n_scored)
+            has = prev.psm["pid"][:, 0] != 0xFFFFFFFF
+            assert np.all(r.psm["key"][has, 0] >= prev.psm["key"][has, 0])
+        prev = r
