@@ -86,7 +86,14 @@ typedef struct hicops_params {
     double min_mass, max_mass;
     double frag_mz_min, frag_mz_max, bin_width_da;
     uint32_t top_n_peaks, min_shared, top_k, hist_bins;
-    uint32_t intensity_scale, reserved;
+    uint32_t intensity_scale;
+    /* Fragment tolerance in bins (dF = tol_bins * bin_width_da on a finer
+     * grid; Experimental Setup's dF): a retained peak in bin b covers bins
+     * b - tol_bins .. b + tol_bins, and an ion bin is shared iff some
+     * retained peak covers it; it counts once, with the largest quantised
+     * intensity of the peaks covering it.  0 = equal bins.  Requires
+     * (2 * tol_bins + 1) * top_n_peaks <= 1024 (HICOPS_EINVAL otherwise). */
+    uint32_t tol_bins;
 } hicops_params;
 
 /* Protein database: n_proteins sequences, protein i = seq[off[i] .. off[i+1]). */

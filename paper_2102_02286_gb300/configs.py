@@ -141,5 +141,17 @@ SERVING_STREAM = Workload(
     description="open_large index; Poisson batches of 1-4096 spectra, 50-500 peaks, +-10/500 Da",
 )
 
-WORKLOADS: List[Workload] = [TINY_CLOSED, OPEN_MEDIUM, OPEN_LARGE, UNEVEN_BATCHED, SERVING_STREAM]
+# the fragment tolerance of t bins on a finer grid: open_medium's database
+# binned at 0.005 Da, each retained peak covering its bin +-1 (dF = 0.005 Da,
+# the paper's experiments' fragment tolerance)
+OPEN_MEDIUM_TOL = Workload(
+    name="open_medium_tol", index=5, n_proteins=20_000, db_index=1,
+    mods=(CARBAMIDOMETHYL_C, OX_M(2), PHOSPHO_STY(1)),
+    params=SearchParams(missed_cleavages=2, bin_width_da=0.005, tol_bins=1, top_n_peaks=100, min_shared=4,
+                        top_k=5),
+    spectra=SpectraRecipe(n_spectra=100_000, target_peaks=(100, 100), charges=(2, 3), tol_da=(500.0,)),
+    description="open_medium database at a 0.005 Da grid, +-1 bin (dF 0.005 Da); 100k spectra x 100 peaks, +-500 Da, top-5",
+)
+
+WORKLOADS: List[Workload] = [TINY_CLOSED, OPEN_MEDIUM, OPEN_LARGE, UNEVEN_BATCHED, SERVING_STREAM, OPEN_MEDIUM_TOL]
 BY_NAME = {w.name: w for w in WORKLOADS}

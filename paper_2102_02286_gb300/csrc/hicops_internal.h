@@ -17,7 +17,7 @@ constexpr double kProtonDa = 1.007276466812;
 constexpr uint32_t kMaxLen = 64;
 constexpr uint32_t kHistBins = 256;
 constexpr uint32_t kMaxTopK = 32;
-constexpr uint32_t kMaxTopN = 1024;
+constexpr uint32_t kMaxTopN = 1024;   // query bins per spectrum (after the tolerance widening)
 
 // The search walks peptide ids in chunks of 2^kChunkShift; every bucket
 // stores where each chunk starts (the skip table).
@@ -32,6 +32,9 @@ constexpr uint32_t kHotShift = 6;
 constexpr uint32_t kNbShift = 26;
 constexpr uint32_t kNyShift = 20;
 constexpr uint32_t kSMask = (1u << 20) - 1;
+
+// Query bins per spectrum: every retained peak widened to 2 t + 1 bins.
+inline uint32_t query_bins_cap(const hicops_params& p) { return (2 * p.tol_bins + 1) * p.top_n_peaks; }
 
 // Thread-local error message (host.cpp).
 void set_error(const char* fmt, ...);

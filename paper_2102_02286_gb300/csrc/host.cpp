@@ -57,12 +57,17 @@ hicops_status validate_params(const hicops_params* p) {
         set_error("top_n_peaks must be in [1, %u]", kMaxTopN);
         return HICOPS_EINVAL;
     }
+    if (p->tol_bins >= kMaxTopN || (uint64_t)(2 * p->tol_bins + 1) * p->top_n_peaks > kMaxTopN) {
+        set_error("(2 * tol_bins + 1) * top_n_peaks must be <= %u", kMaxTopN);
+        return HICOPS_EINVAL;
+    }
     if (p->hist_bins != kHistBins) { set_error("hist_bins must be %u", kHistBins); return HICOPS_EINVAL; }
     if (p->intensity_scale < 1) { set_error("intensity_scale must be >= 1"); return HICOPS_EINVAL; }
     if (p->min_shared < 1) { set_error("min_shared must be >= 1"); return HICOPS_EINVAL; }
-    const uint64_t max_matched = std::min<uint64_t>(p->top_n_peaks, 2ull * (p->max_len - 1));
+    // a peptide shares at most one ion per query bin
+    const uint64_t max_matched = std::min<uint64_t>(query_bins_cap(*p), 2ull * (p->max_len - 1));
     if (max_matched * p->intensity_scale > kSMask) {
-        set_error("min(top_n_peaks, 2*(max_len-1)) * intensity_scale must be < 2^20");
+        set_error("min((2*tol_bins+1)*top_n_peaks, 2*(max_len-1)) * intensity_scale must be < 2^20");
         return HICOPS_EOVERFLOW;
     }
     if (!(p->min_mass <= p->max_mass)) { set_error("min_mass > max_mass"); return HICOPS_EINVAL; }
@@ -325,7 +330,7 @@ extern "C" hicops_status hicops_digest(const hicops_proteins* prot, const hicops
     });
 
     idx->n_bins = (uint32_t)std::floor(p.frag_mz_max / p.bin_width_da) + 1;
-    idx->s_max = std::min<uint64_t>(p.top_n_peaks, 2ull * (p.max_len - 1)) * p.intensity_scale;
+    idx->s_max = std::min<uint64_t>(query_bins_cap(p), 2ull * (p.max_len - 1)) * p.intensity_scale;
     idx->stats.n_peptides = total;
     idx->stats.n_base_peptides = NB;
     idx->stats.n_bins = idx->n_bins;

@@ -80,8 +80,8 @@ hicops_status alloc_workspace(A& al, const hicops_params& p, uint32_t cap_n, uin
                               Workspace& w) {
     w.cap_n = cap_n;
     w.max_seg = max_seg;
-    HC_CUDA(al.get(&w.qbin, (uint64_t)cap_n * p.top_n_peaks));
-    HC_CUDA(al.get(&w.qiq, (uint64_t)cap_n * p.top_n_peaks));
+    HC_CUDA(al.get(&w.qbin, (uint64_t)cap_n * query_bins_cap(p)));
+    HC_CUDA(al.get(&w.qiq, (uint64_t)cap_n * query_bins_cap(p)));
     HC_CUDA(al.get(&w.qn, cap_n));
     HC_CUDA(al.get(&w.lo, cap_n));
     HC_CUDA(al.get(&w.hi, cap_n));
@@ -179,6 +179,29 @@ inline void mark(hicops_index* idx, int i, cudaStream_t s, bool on) {
     if (on && idx->dev.timing) cudaEventRecord((cudaEvent_t)idx->dev.ev[i], s);
 }
 
+// Query preprocessing of n spectra (R8), then, with a fragment tolerance of
+// t > 0 bins, the widening of every spectrum's bins (R15).  qbin / qiq hold
+// query_bins_cap(p) words per spectrum.
+hicops_status prepare_queries(hicops_index* idx, const DevBatch& d, uint32_t n, uint32_t* qbin, uint32_t* qiq,
+                              uint32_t* qn, uint32_t* lo, uint32_t* hi, cudaStream_t s) {
+    const hicops_params& p = idx->p;
+    const uint32_t stride = query_bins_cap(p);
+    PrepArgs pa{d.peak_off, d.mz, d.inten, d.prec, d.z, d.tol, n, p.top_n_peaks, stride, p.bin_width_da,
+                p.frag_mz_min, p.frag_mz_max, (double)p.intensity_scale, idx->dev.mass, idx->mass.size(),
+                qbin, qiq, qn, lo, hi};
+    prep_warp_kernel<<<(n + kPrepWarps - 1) / kPrepWarps, kPrepWarps * 32, 0, s>>>(pa);
+    prep_kernel<<<n, kPrepThreads, 0, s>>>(pa);   // spectra of more than kPrepWarpPeaks peaks
+    count_launches(2);
+    HC_CUDA(cudaGetLastError());
+    if (p.tol_bins > 0) {
+        ExpandArgs ea{qbin, qiq, qn, n, stride, p.tol_bins, idx->n_bins};
+        expand_kernel<<<(n + kExpWarps - 1) / kExpWarps, kExpWarps * 32, 0, s>>>(ea);
+        count_launches(1);
+        HC_CUDA(cudaGetLastError());
+    }
+    return HICOPS_OK;
+}
+
 // The whole search of n spectra on stream s, writing PSM rows, histograms
 // and candidate counts to device memory.  Allocates nothing.
 hicops_status enqueue_search(hicops_index* idx, const DevBatch& d, uint32_t n, const Workspace& w,
@@ -189,12 +212,8 @@ hicops_status enqueue_search(hicops_index* idx, const DevBatch& d, uint32_t n, c
     const hicops_search_config cfg = resolved(cfg_in, idx->p.top_k);
     const uint32_t k = p.top_k;
     mark(idx, 0, s, timing_marks);
-    PrepArgs pa{d.peak_off, d.mz, d.inten, d.prec, d.z, d.tol, n, p.top_n_peaks, p.bin_width_da, p.frag_mz_min,
-                p.frag_mz_max, (double)p.intensity_scale, di.mass, idx->mass.size(), w.qbin, w.qiq, w.qn, w.lo, w.hi};
-    prep_warp_kernel<<<(n + kPrepWarps - 1) / kPrepWarps, kPrepWarps * 32, 0, s>>>(pa);
-    prep_kernel<<<n, kPrepThreads, 0, s>>>(pa);   // spectra of more than kPrepWarpPeaks peaks
-    count_launches(2);
-    HC_CUDA(cudaGetLastError());
+    hicops_status st = prepare_queries(idx, d, n, w.qbin, w.qiq, w.qn, w.lo, w.hi, s);
+    if (st != HICOPS_OK) return st;
     mark(idx, 1, s, timing_marks);
     const uint32_t max_seg = w.max_seg;
     const uint32_t seg_pids = cfg.seg_pids ? cfg.seg_pids : (uint32_t)kMinSegPids;
@@ -205,12 +224,12 @@ hicops_status enqueue_search(hicops_index* idx, const DevBatch& d, uint32_t n, c
     HC_CUDA(cudaMemsetAsync(d_hist, 0, sizeof(uint32_t) * n * kHistBins, s));
     HC_CUDA(cudaMemsetAsync(d_ns, 0, sizeof(uint32_t) * n, s));
     HC_CUDA(cudaMemsetAsync(w.work, 0, sizeof(unsigned long long), s));
-    SearchArgs sa{w.qbin, w.qiq, w.qn, w.lo, w.hi, w.seg_off, n, p.top_n_peaks, di.off, di.entry,
+    SearchArgs sa{w.qbin, w.qiq, w.qn, w.lo, w.hi, w.seg_off, n, query_bins_cap(p), di.off, di.entry,
                   di.skip_row, di.skip, di.skip_stride, di.hot_id, di.hot_b, di.hot_y, di.hot_flags,
                   di.hot_words, di.lf, di.ls, (uint32_t)idx->s_max, p.min_shared, k, cfg.chunk_entries * 1024u, w.utop, d_hist, d_ns,
                   w.work};
     mark(idx, 2, s, timing_marks);
-    hicops_status st = launch_search(sa, cfg, (uint64_t)n * max_seg, s);
+    st = launch_search(sa, cfg, (uint64_t)n * max_seg, s);
     if (st != HICOPS_OK) return st;
     mark(idx, 3, s, timing_marks);
     MergeArgs ma{w.seg_off, w.utop, d_hist, n, k, 0, d_psm, idx->pid_stride, idx->pid_base};
@@ -342,20 +361,15 @@ extern "C" hicops_status hicops_search_work(hicops_index* idx, const hicops_batc
         if (st != HICOPS_OK) return st;
         uint32_t *qbin, *qiq, *qn, *lo, *hi;
         uint64_t* hits;
-        HC_CUDA(sc.get(&qbin, (uint64_t)n * p.top_n_peaks));
-        HC_CUDA(sc.get(&qiq, (uint64_t)n * p.top_n_peaks));
+        HC_CUDA(sc.get(&qbin, (uint64_t)n * query_bins_cap(p)));
+        HC_CUDA(sc.get(&qiq, (uint64_t)n * query_bins_cap(p)));
         HC_CUDA(sc.get(&qn, n));
         HC_CUDA(sc.get(&lo, n));
         HC_CUDA(sc.get(&hi, n));
         HC_CUDA(sc.get(&hits, n));
-        PrepArgs pa{d.peak_off, d.mz, d.inten, d.prec, d.z, d.tol, n, p.top_n_peaks, p.bin_width_da,
-                    p.frag_mz_min, p.frag_mz_max, (double)p.intensity_scale, idx->dev.mass, idx->mass.size(),
-                    qbin, qiq, qn, lo, hi};
-        prep_warp_kernel<<<(n + kPrepWarps - 1) / kPrepWarps, kPrepWarps * 32, 0, s>>>(pa);
-        prep_kernel<<<n, kPrepThreads, 0, s>>>(pa);
-        count_launches(2);
-        HC_CUDA(cudaGetLastError());
-        work_kernel<<<n, 256, 0, s>>>(qbin, qn, lo, hi, p.top_n_peaks, idx->dev.off, idx->dev.entry, hits);
+        st = prepare_queries(idx, d, n, qbin, qiq, qn, lo, hi, s);
+        if (st != HICOPS_OK) return st;
+        work_kernel<<<n, 256, 0, s>>>(qbin, qn, lo, hi, query_bins_cap(p), idx->dev.off, idx->dev.entry, hits);
         count_launches(1);
         HC_CUDA(cudaGetLastError());
         const cudaMemcpyKind kind = b->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;

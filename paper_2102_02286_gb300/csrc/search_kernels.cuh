@@ -33,12 +33,13 @@ struct PrepArgs {
     const uint8_t* charge;
     const double* tol;
     uint32_t n;
-    uint32_t topn;
+    uint32_t topn;      // peaks retained
+    uint32_t stride;    // qbin / qiq words per spectrum (>= topn)
     double w, mz_lo, mz_hi, scale;
     const double* mass;
     uint64_t P;
-    uint32_t* qbin;     // [n * topn]
-    uint32_t* qiq;      // [n * topn]
+    uint32_t* qbin;     // [n * stride]
+    uint32_t* qiq;      // [n * stride]
     uint32_t* qn;       // [n]
     uint32_t* lo;       // [n]
     uint32_t* hi;       // [n]
@@ -132,8 +133,8 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(PrepArgs a) {
                 const uint64_t k = keys[t];
                 const double I = (double)__uint_as_float(~(uint32_t)(k >> 32));
                 const double r = floor(__dmul_rn(I, a.scale) / Imax);
-                a.qbin[(uint64_t)q * a.topn + t] = (uint32_t)k;
-                a.qiq[(uint64_t)q * a.topn + t] = r < 1.0 ? 1u : (uint32_t)r;
+                a.qbin[(uint64_t)q * a.stride + t] = (uint32_t)k;
+                a.qiq[(uint64_t)q * a.stride + t] = r < 1.0 ? 1u : (uint32_t)r;
             }
         }
     }
@@ -231,8 +232,8 @@ __global__ void __launch_bounds__(kPrepWarps * 32) prep_warp_kernel(PrepArgs a) 
                 const uint64_t k = keys[t];
                 const double I = (double)__uint_as_float(~(uint32_t)(k >> 32));
                 const double r = floor(__dmul_rn(I, a.scale) / Imax);
-                a.qbin[(uint64_t)q * a.topn + t] = (uint32_t)k;
-                a.qiq[(uint64_t)q * a.topn + t] = r < 1.0 ? 1u : (uint32_t)r;
+                a.qbin[(uint64_t)q * a.stride + t] = (uint32_t)k;
+                a.qiq[(uint64_t)q * a.stride + t] = r < 1.0 ? 1u : (uint32_t)r;
             }
         }
     }
@@ -424,6 +425,71 @@ __global__ void __launch_bounds__(kMergeWarps * 32) merge_kernel(MergeArgs a) {
 }
 
 // per spectrum: sum over retained peaks of the bucket entries inside [lo, hi)
+// Fragment tolerance of t bins (R15): replaces spectrum q's retained peaks
+// (distinct bins in any order) by the union of their windows [b - t, b + t]
+// cut to [0, n_bins), ascending, each bin with the largest iq of the peaks
+// covering it.  One warp per spectrum, in place: the peaks are read into
+// shared memory and sorted by bin first.  Peak i emits the bins of its
+// window above the previous peak's window, so no bin is emitted twice, and
+// only peaks j >= i can cover them.
+constexpr int kExpWarps = 4;
+
+struct ExpandArgs {
+    uint32_t* qbin;
+    uint32_t* qiq;
+    uint32_t* qn;
+    uint32_t n, stride, t, n_bins;
+};
+
+__global__ void __launch_bounds__(kExpWarps * 32) expand_kernel(ExpandArgs a) {
+    __shared__ uint64_t keys_all[kExpWarps][kMaxTopN];
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    const uint32_t q = blockIdx.x * kExpWarps + wi;
+    if (q >= a.n) return;   // warp-uniform
+    const uint32_t cnt = a.qn[q];
+    if (cnt == 0) return;
+    uint64_t* keys = keys_all[wi];
+    uint32_t* qb = a.qbin + (uint64_t)q * a.stride;
+    uint32_t* qi = a.qiq + (uint64_t)q * a.stride;
+    const int npow = next_pow2((int)cnt);
+    for (int i = lane; i < npow; i += 32) keys[i] = i < (int)cnt ? ((uint64_t)qb[i] << 32) | qi[i] : ~0ull;
+    __syncwarp();
+    warp_bitonic_sort_u64(keys, npow, lane);
+    const uint32_t t = a.t;
+    uint32_t base = 0;
+    for (uint32_t i0 = 0; i0 < cnt; i0 += 32) {   // warp-uniform trip count
+        const uint32_t i = i0 + lane;
+        uint32_t lo = 0, hi = 0;   // bins [lo, hi) emitted by peak i
+        if (i < cnt) {
+            const uint32_t b = (uint32_t)(keys[i] >> 32);
+            lo = b > t ? b - t : 0u;
+            if (i > 0) lo = max(lo, (uint32_t)(keys[i - 1] >> 32) + t + 1u);
+            hi = min(b + t + 1u, a.n_bins);
+            if (hi < lo) hi = lo;
+        }
+        const uint32_t len = hi - lo;
+        uint32_t incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t x = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += x;
+        }
+        const uint32_t pos = base + incl - len;
+        base += __shfl_sync(0xffffffffu, incl, 31);
+        for (uint32_t x = lo; x < hi; ++x) {
+            uint32_t best = 0;
+            for (uint32_t j = i; j < cnt; ++j) {
+                const uint64_t kj = keys[j];
+                if ((uint32_t)(kj >> 32) > x + t) break;
+                best = max(best, (uint32_t)kj);
+            }
+            qb[pos + (x - lo)] = x;
+            qi[pos + (x - lo)] = best;
+        }
+    }
+    if (lane == 0) a.qn[q] = base;
+}
+
 __global__ void work_kernel(const uint32_t* __restrict__ qbin, const uint32_t* __restrict__ qn,
                             const uint32_t* __restrict__ lo, const uint32_t* __restrict__ hi, uint32_t topn,
                             const uint64_t* __restrict__ off, const uint32_t* __restrict__ entry,

@@ -268,7 +268,7 @@ extern "C" hicops_status hicops_server_create(hicops_index* idx, const hicops_se
     // units, per-unit top-k, rows, histogram) plus staged inputs (up to
     // 512 peaks per spectrum before it grows)
     const hicops_params& p = idx->p;
-    const uint64_t per_spec = 8ull * p.top_n_peaks + 48 + 64ull * p.top_k * 16 + p.top_k * 32ull * 2 +
+    const uint64_t per_spec = 8ull * hicops::query_bins_cap(p) + 48 + 64ull * p.top_k * 16 + p.top_k * 32ull * 2 +
                               2 * 4 * hicops::kHistBins + 8 + 512ull * 8 + 17;
     const uint64_t slot_bytes = per_spec * cfg.slot_spectra;
     uint64_t n_slots = cfg.memory_budget / (slot_bytes ? slot_bytes : 1);

@@ -38,7 +38,7 @@ class Params(C.Structure):
                 ("max_total_mods", C.c_uint32), ("min_mass", C.c_double), ("max_mass", C.c_double),
                 ("frag_mz_min", C.c_double), ("frag_mz_max", C.c_double), ("bin_width_da", C.c_double),
                 ("top_n_peaks", C.c_uint32), ("min_shared", C.c_uint32), ("top_k", C.c_uint32),
-                ("hist_bins", C.c_uint32), ("intensity_scale", C.c_uint32), ("reserved", C.c_uint32)]
+                ("hist_bins", C.c_uint32), ("intensity_scale", C.c_uint32), ("tol_bins", C.c_uint32)]
 
 
 class Proteins(C.Structure):
@@ -159,7 +159,7 @@ def make_params(sp) -> Params:
                   max_total_mods=sp.max_total_mods, min_mass=sp.min_mass, max_mass=sp.max_mass,
                   frag_mz_min=sp.frag_mz_min, frag_mz_max=sp.frag_mz_max, bin_width_da=sp.bin_width_da,
                   top_n_peaks=sp.top_n_peaks, min_shared=sp.min_shared, top_k=sp.top_k,
-                  hist_bins=sp.hist_bins, intensity_scale=sp.intensity_scale, reserved=0)
+                  hist_bins=sp.hist_bins, intensity_scale=sp.intensity_scale, tol_bins=sp.tol_bins)
 
 
 @dataclass
