@@ -42,7 +42,7 @@ class OrParams(C.Structure):
                 ("frag_mz_min", C.c_double), ("frag_mz_max", C.c_double), ("bin_width", C.c_double),
                 ("top_n_peaks", C.c_uint32), ("min_shared", C.c_uint32), ("top_k", C.c_uint32),
                 ("hist_bins", C.c_uint32), ("intensity_scale", C.c_uint32), ("max_total_mods", C.c_uint32),
-                ("tol_bins", C.c_uint32), ("pad1", C.c_uint32)]
+                ("tol_bins", C.c_uint32), ("evalue_mode", C.c_uint32)]
 
 
 PSM_DTYPE = np.dtype([("pid", np.uint32), ("nb", np.uint32), ("ny", np.uint32), ("S", np.uint32),
@@ -76,7 +76,7 @@ def lib():
         L.or_rank_key.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32]
         L.or_hyperscore.restype = C.c_double
         L.or_hyperscore.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32]
-        L.or_evalue.argtypes = [P, C.c_uint32, P, P, C.c_uint32, P]
+        L.or_evalue.argtypes = [P, C.c_uint32, P, P, C.c_uint32, C.c_uint32, P]
         L.or_search.argtypes = [P, P, P, P, P, P, P, P, C.c_uint32, P, P, P, P, P]
         L.or_search_shard.argtypes = [P, P, P, P, P, P, P, P, C.c_uint32, P, P, P, P, P, C.c_uint32, C.c_uint32]
     return _lib
@@ -93,7 +93,7 @@ def make_params(sp) -> OrParams:
                     frag_mz_max=sp.frag_mz_max, bin_width=sp.bin_width_da, top_n_peaks=sp.top_n_peaks,
                     min_shared=sp.min_shared, top_k=sp.top_k, hist_bins=sp.hist_bins,
                     intensity_scale=sp.intensity_scale, max_total_mods=sp.max_total_mods,
-                    tol_bins=sp.tol_bins, pad1=0)
+                    tol_bins=sp.tol_bins, evalue_mode=sp.evalue_mode)
 
 
 @dataclass
@@ -194,10 +194,10 @@ def hyperscore(nb, ny, S) -> float:
     return float(lib().or_hyperscore(nb, ny, S))
 
 
-def evalue(hist, keys, pids) -> np.ndarray:
+def evalue(hist, keys, pids, evalue_mode=0) -> np.ndarray:
     hist = np.ascontiguousarray(hist, np.uint32)
     keys = np.ascontiguousarray(keys, np.int64)
     pids = np.ascontiguousarray(pids, np.uint32)
     out = np.zeros(len(keys), np.float64)
-    lib().or_evalue(_ptr(hist), len(hist), _ptr(keys), _ptr(pids), len(keys), _ptr(out))
+    lib().or_evalue(_ptr(hist), len(hist), _ptr(keys), _ptr(pids), len(keys), evalue_mode, _ptr(out))
     return out

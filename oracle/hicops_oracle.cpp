@@ -51,7 +51,14 @@
 //   R11 histogram bin = min(255, K >> 31) over every candidate;
 //   R12 e-value: survival s_j = sum_{i>=j} hist_i; least-squares line through
 //      (j, log10(s_j / N)) for j in [mode+1, jtop-1] with s_j > 0; e = N *
-//      10^(w * K*2^-31 + b); fewer than 3 points -> e = N.
+//      10^(w * K*2^-31 + b); fewer than 3 points -> e = N;
+//   R16 (optional) the fit sees the histogram smoothed by the 5-point
+//      quadratic Savitzky-Golay filter (taps -3 12 17 12 -3 over 35, zero
+//      outside the bins), kept as 35 times its value so it stays integer;
+//   R17 (optional, instead of R12) log-Weibull (Gumbel) fit: least squares
+//      of -ln(-ln F_j) on x = j + 1, F_j = fraction scoring below j + 1, over
+//      bins with 0 < F_j < 1; e = N * (1 - exp(-exp(-(a x + c)))), x =
+//      K*2^-31; fewer than 3 points or a <= 0 -> e = N.
 //
 // Parity pins: see tests/test_oracle_pins.py (closed forms, elemental
 // composition masses, brute force on tiny inputs, invariants).  Parity
@@ -105,7 +112,8 @@ struct OrParams {
     double frag_mz_min, frag_mz_max, bin_width;
     uint32_t top_n_peaks, min_shared, top_k, hist_bins;
     uint32_t intensity_scale, max_total_mods;
-    uint32_t tol_bins, pad1;   // R15 fragment tolerance in bins (0 = R6)
+    uint32_t tol_bins;         // R15 fragment tolerance in bins (0 = R6)
+    uint32_t evalue_mode;      // bit 0: R17 log-Weibull fit (else R12), bit 1: R16 smoothing
 };
 
 // One PSM row of the oracle's output.
@@ -284,20 +292,65 @@ int64_t rank_key(uint32_t nb, uint32_t ny, uint32_t S) {
            std::llround(std::ldexp(std::log10((double)S), 32));
 }
 
-// R12
-void evalues(const uint32_t* hist, uint32_t nbins, const std::vector<OrPsm>& top, std::vector<double>& ev) {
+// R12 (linear tail fit), R16 (Savitzky-Golay smoothing first), R17
+// (log-Weibull fit instead of the tail fit)
+void evalues(const uint32_t* hist, uint32_t nbins, const std::vector<OrPsm>& top, uint32_t ev_mode,
+             std::vector<double>& ev) {
     ev.assign(top.size(), INFINITY);
     if (top.empty() || top[0].pid == UINT32_MAX) return;
-    std::vector<double> s(nbins + 1, 0.0);
-    for (int j = (int)nbins - 1; j >= 0; --j) s[j] = s[j + 1] + (double)hist[j];
-    const double N = s[0];
-    uint32_t mode = 0;
-    for (uint32_t j = 1; j < nbins; ++j) if (hist[j] > hist[mode]) mode = j;
-    const int64_t jtop = std::min<int64_t>(nbins - 1, top[0].key >> 31);
+    double N = 0.0;
+    for (uint32_t j = 0; j < nbins; ++j) N += (double)hist[j];
+    // the distribution the fit sees: the histogram, or (R16) 35 times its
+    // 5-point quadratic Savitzky-Golay smoothing, the histogram taken as 0
+    // outside its bins; integers either way
+    std::vector<int64_t> g(nbins, 0);
+    for (int64_t j = 0; j < (int64_t)nbins; ++j) {
+        if (!(ev_mode & 2u)) { g[j] = hist[j]; continue; }
+        static const int64_t c[5] = {-3, 12, 17, 12, -3};
+        for (int d = -2; d <= 2; ++d) {
+            const int64_t i = j + d;
+            if (i >= 0 && i < (int64_t)nbins) g[j] += c[d + 2] * (int64_t)hist[i];
+        }
+    }
+    std::vector<int64_t> G(nbins + 1, 0);   // G[j] = sum of g[i >= j]
+    for (int64_t j = (int64_t)nbins - 1; j >= 0; --j) G[j] = G[j + 1] + g[j];
+    const double G0 = (double)G[0];
     double n = 0, sx = 0, sy = 0, sxx = 0, sxy = 0;
+    if (ev_mode & 1u) {
+        // R17: the log-Weibull (Gumbel) CDF F(x) = exp(-exp(-(a x + c)))
+        // fitted by least squares of -ln(-ln F_j) on x = j + 1, where F_j =
+        // 1 - G[j + 1] / G[0] is the fraction scoring below j + 1, over the
+        // bins with 0 < F_j < 1
+        for (uint32_t j = 0; j < nbins; ++j) {
+            if (!(G[j + 1] > 0 && G[j + 1] < G[0])) continue;
+            const double x = (double)(j + 1);
+            const double yv = -std::log(-std::log1p(-((double)G[j + 1] / G0)));
+            n += 1; sx += x; sy += yv; sxx += x * x; sxy += x * yv;
+        }
+        double a = 0, c = 0;
+        bool fit = n >= 3;
+        if (fit) {
+            const double den = n * sxx - sx * sx;
+            a = (n * sxy - sx * sy) / den;
+            c = (sy - a * sx) / n;
+            fit = a > 0;
+        }
+        for (size_t r = 0; r < top.size(); ++r) {
+            if (top[r].pid == UINT32_MAX) continue;
+            if (!fit) { ev[r] = N; continue; }
+            const double x = std::ldexp((double)top[r].key, -31);
+            ev[r] = N * -std::expm1(-std::exp(-(a * x + c)));   // N * P(score >= x)
+        }
+        return;
+    }
+    // R12 on g: survival G[j] / G[0]; line through (j, log10 of it) for j in
+    // [mode + 1, jtop - 1] with G[j] > 0; mode = the largest g, lowest bin
+    uint32_t mode = 0;
+    for (uint32_t j = 1; j < nbins; ++j) if (g[j] > g[mode]) mode = j;
+    const int64_t jtop = std::min<int64_t>(nbins - 1, top[0].key >> 31);
     for (int64_t j = mode + 1; j <= jtop - 1; ++j) {
-        if (!(s[j] > 0.0)) continue;
-        double x = (double)j, yv = std::log10(s[j] / N);
+        if (!(G[j] > 0)) continue;
+        double x = (double)j, yv = std::log10((double)G[j] / G0);
         n += 1; sx += x; sy += yv; sxx += x * x; sxy += x * yv;
     }
     bool fit = n >= 3;
@@ -420,13 +473,14 @@ double or_hyperscore(uint32_t nb, uint32_t ny, uint32_t S) {
     return log10_factorial(nb) + log10_factorial(ny) + std::log10((double)S);
 }
 
-// e-values for a given histogram and sorted top-k keys (R12).
+// e-values for a given histogram and sorted top-k keys (R12; ev_mode bit 0
+// R17, bit 1 R16).
 void or_evalue(const uint32_t* hist, uint32_t nbins, const int64_t* keys, const uint32_t* pids,
-               uint32_t k, double* out) {
+               uint32_t k, uint32_t ev_mode, double* out) {
     std::vector<OrPsm> top(k);
     for (uint32_t i = 0; i < k; ++i) { top[i].key = keys[i]; top[i].pid = pids[i]; }
     std::vector<double> ev;
-    evalues(hist, nbins, top, ev);
+    evalues(hist, nbins, top, ev_mode, ev);
     for (uint32_t i = 0; i < k; ++i) out[i] = ev[i];
 }
 
@@ -496,7 +550,7 @@ void or_search_shard(void* h, const uint64_t* peak_off, const float* mz, const f
                    top[r].key = INT64_MIN; top[r].hyperscore = 0; top[r].evalue = INFINITY; }
         }
         std::vector<double> ev;
-        evalues(hist, H, top, ev);
+        evalues(hist, H, top, p.evalue_mode, ev);
         for (uint32_t r = 0; r < K; ++r) { top[r].evalue = ev[r]; out_psm[(uint64_t)si * K + r] = top[r]; }
         out_nscored[si] = (uint32_t)cand.size();
         if (out_lo) out_lo[si] = lo;

@@ -55,6 +55,9 @@ class SearchParams:
     top_k: int = 5
     hist_bins: int = 256
     intensity_scale: int = 10000
+    # e-value: bit 0 = log-Weibull (Gumbel) fit instead of the linear tail
+    # fit, bit 1 = Savitzky-Golay smoothing of the histogram before the fit
+    evalue_mode: int = 0
     max_total_mods: int = 0        # 0 = no global cap
 
 

@@ -424,7 +424,6 @@ __global__ void __launch_bounds__(kMergeWarps * 32) merge_kernel(MergeArgs a) {
     }
 }
 
-// per spectrum: sum over retained peaks of the bucket entries inside [lo, hi)
 // Fragment tolerance of t bins (R15): replaces spectrum q's retained peaks
 // (distinct bins in any order) by the union of their windows [b - t, b + t]
 // cut to [0, n_bins), ascending, each bin with the largest iq of the peaks
@@ -490,6 +489,7 @@ __global__ void __launch_bounds__(kExpWarps * 32) expand_kernel(ExpandArgs a) {
     if (lane == 0) a.qn[q] = base;
 }
 
+// per spectrum: sum over retained peaks of the bucket entries inside [lo, hi)
 __global__ void work_kernel(const uint32_t* __restrict__ qbin, const uint32_t* __restrict__ qn,
                             const uint32_t* __restrict__ lo, const uint32_t* __restrict__ hi, uint32_t topn,
                             const uint64_t* __restrict__ off, const uint32_t* __restrict__ entry,

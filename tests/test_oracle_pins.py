@@ -13,6 +13,11 @@
   enumeration, ordering and all-pairs matching code);
 * invariants: shared counts <= min(query bins, peptide bins), window
   monotonicity, and the self-match of a noise-free spectrum;
+* the e-value variants: the Savitzky-Golay smoothing (R16) against scipy's
+  savgol_filter with the tail fit done by numpy's polyfit, the log-Weibull
+  fit (R17) against numpy's polyfit and scipy's Gumbel survival function,
+  and the recovery of a known Gumbel's location and scale from its binned
+  counts;
 * the fragment tolerance of t bins (R15): a hand-worked spectrum with peaks
   one and two bins off the ions and two peaks covering one ion, the brute
   force above with every (ion, peak) pair compared by bin distance, the
@@ -608,3 +613,85 @@ def test_tolerance_monotone(oracle_lib, tiny):
             has = prev.psm["pid"][:, 0] != 0xFFFFFFFF
             assert np.all(r.psm["key"][has, 0] >= prev.psm["key"][has, 0])
         prev = r
+
+
+# ---------------------------------------------------------------- R16, R17
+
+
+def _keys(xs):
+    return np.array([int(round(x * 2 ** 31)) for x in xs], np.int64)
+
+
+def _binned_gumbel(mu, beta, m):
+    from scipy.stats import gumbel_r
+    f = gumbel_r.cdf(np.arange(257, dtype=float), loc=mu, scale=beta)
+    return np.rint(m * np.diff(f)).astype(np.uint32)
+
+
+def _fit_points(g, ev_mode, jtop):
+    """(x, y) of the fit from the fit's histogram g (numpy)."""
+    G = np.concatenate([np.cumsum(g[::-1])[::-1], [0]]).astype(np.float64)
+    if ev_mode & 1:
+        sel = (G[1:] > 0) & (G[1:] < G[0])
+        return np.arange(1, 257)[sel].astype(float), -np.log(-np.log1p(-(G[1:][sel] / G[0])))
+    mode = int(np.argmax(g))
+    j = np.arange(256)
+    sel = (j >= mode + 1) & (j <= jtop - 1) & (G[:256] > 0)
+    return j[sel].astype(float), np.log10(G[:256][sel] / G[0])
+
+
+@pytest.mark.parametrize("ev_mode", [1, 2, 3])
+def test_evalue_variants_against_library_routines(oracle_lib, ev_mode):
+    signal = pytest.importorskip("scipy.signal")
+    from scipy.stats import gumbel_r
+    rng = np.random.default_rng(ev_mode)
+    for trial in range(4):
+        h = _binned_gumbel(25.0 + 10 * trial, 3.0 + trial, 10 ** (5 + trial))
+        h[int(rng.integers(5, 60))] += np.uint32(rng.integers(1000, 50000))   # a spike the smoothing spreads
+        xs = [float(v) for v in np.sort(rng.uniform(30, 90, 5))[::-1]]
+        keys = _keys(xs)
+        pids = np.arange(5, dtype=np.uint32)
+        got = oracle_lib.evalue(h, keys, pids, ev_mode)
+        g = h.astype(np.float64)
+        if ev_mode & 2:   # 35 x the 5-point quadratic smoothing, zero outside
+            g = np.rint(35 * signal.savgol_filter(g, 5, 2, mode="constant", cval=0.0))
+            assert np.allclose(signal.savgol_coeffs(5, 2) * 35, [-3, 12, 17, 12, -3])
+        x, y = _fit_points(g, ev_mode, min(255, int(keys[0]) >> 31))
+        N = float(h.sum())
+        a, c = np.polyfit(x, y, 1)
+        if ev_mode & 1:
+            want = N * gumbel_r.sf(np.asarray(xs), loc=-c / a, scale=1 / a)
+        else:
+            want = N * 10 ** (a * np.asarray(xs) + c)
+        np.testing.assert_allclose(got, want, rtol=1e-8)
+    # the smoothing changes the answer
+    h = _binned_gumbel(30.0, 3.0, 10 ** 6)
+    h[20] += np.uint32(40000)
+    k = _keys([60.0])
+    one = np.zeros(1, np.uint32)
+    assert oracle_lib.evalue(h, k, one, ev_mode)[0] != oracle_lib.evalue(h, k, one, ev_mode ^ 2)[0]
+
+
+@pytest.mark.parametrize("mu,beta,m", [(40.0, 4.0, 4e9), (30.0, 2.5, 1e8), (60.0, 6.0, 1e6)])
+def test_log_weibull_fit_recovers_a_binned_gumbel(oracle_lib, mu, beta, m):
+    pytest.importorskip("scipy")
+    h = _binned_gumbel(mu, beta, m)
+    N = float(h.sum())
+    xs = [mu + 3 * beta, mu]
+    e = oracle_lib.evalue(h, _keys(xs), np.arange(2, dtype=np.uint32), 1)
+    # e = N (1 - exp(-exp(-(x - mu) / beta))): -ln(-ln(1 - e / N)) is linear in x
+    z = -np.log(-np.log1p(-e / N))
+    a = (z[0] - z[1]) / (xs[0] - xs[1])
+    c = z[0] - a * xs[0]
+    assert abs(1 / a - beta) < 0.03 * beta
+    assert abs(-c / a - mu) < 0.5
+
+
+def test_evalue_variant_fallbacks(oracle_lib):
+    # one occupied bin: no point with 0 < F < 1, so e = N; no top hit: +inf
+    h = np.zeros(256, np.uint32)
+    h[30] = 77
+    for mode in (1, 3):
+        assert oracle_lib.evalue(h, _keys([30.2]), np.zeros(1, np.uint32), mode)[0] == 77.0
+        e = oracle_lib.evalue(h, np.array([np.iinfo(np.int64).min], np.int64), np.array([0xFFFFFFFF], np.uint32), mode)
+        assert np.isinf(e[0])
