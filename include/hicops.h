@@ -94,7 +94,17 @@ typedef struct hicops_params {
      * intensity of the peaks covering it.  0 = equal bins.  Requires
      * (2 * tol_bins + 1) * top_n_peaks <= 1024 (HICOPS_EINVAL otherwise). */
     uint32_t tol_bins;
+    /* E-value of the top-k rows from the spectrum's score histogram
+     * (Superstep 4, Supplementary Algorithm 4): 0 = the linear tail fit;
+     * HICOPS_EVALUE_LOG_WEIBULL = the log-Weibull (Gumbel) fit instead;
+     * HICOPS_EVALUE_SMOOTH = either fit on the histogram smoothed by the
+     * 5-point quadratic Savitzky-Golay filter.  Other bits: HICOPS_EINVAL. */
+    uint32_t evalue_mode;
+    uint32_t reserved;   /* 0 */
 } hicops_params;
+
+#define HICOPS_EVALUE_LOG_WEIBULL 1u
+#define HICOPS_EVALUE_SMOOTH 2u
 
 /* Protein database: n_proteins sequences, protein i = seq[off[i] .. off[i+1]). */
 typedef struct hicops_proteins {
@@ -245,15 +255,16 @@ hicops_status hicops_index_shard(const hicops_index* full, uint32_t n_shards, ui
  *   shard_psm [n_shards * n * top_k]: shard s's rows of spectrum q at
  *   (s * n + q) * top_k; hist [hist_parts * n * 256] and nscored
  *   [hist_parts * n]: hist_parts = n_shards (per shard, summed here) or 1
- *   (already summed, e.g. by an all-reduce).  Outputs as hicops_search
+ *   (already summed, e.g. by an all-reduce).  evalue_mode as in hicops_params
+ *   (the shards' own; HICOPS_EINVAL for other bits).  Outputs as hicops_search
  *   (out_hist, out_nscored may be NULL).  on_device = 1: every buffer is a
  *   device buffer and the work is enqueued on cuda_stream; 0: host buffers,
  *   the call copies and waits.  Runs on the current device.
  * Errors: HICOPS_EINVAL (sizes, NULL inputs), HICOPS_ECUDA, HICOPS_ENOMEM. */
 hicops_status hicops_merge_shards(uint32_t n_shards, uint32_t n, uint32_t top_k, const hicops_psm* shard_psm,
                                   const uint32_t* hist, const uint32_t* nscored, uint32_t hist_parts,
-                                  int on_device, void* cuda_stream, hicops_psm* out_psm, uint32_t* out_hist,
-                                  uint32_t* out_nscored);
+                                  uint32_t evalue_mode, int on_device, void* cuda_stream, hicops_psm* out_psm,
+                                  uint32_t* out_hist, uint32_t* out_nscored);
 
 /* Peptide pid: sequence (NUL-terminated, truncated to cap-1 letters), neutral
  * mass and the bitmask of positions carrying a variable modification (bit j =

@@ -62,6 +62,10 @@ hicops_status validate_params(const hicops_params* p) {
         return HICOPS_EINVAL;
     }
     if (p->hist_bins != kHistBins) { set_error("hist_bins must be %u", kHistBins); return HICOPS_EINVAL; }
+    if (p->evalue_mode & ~(HICOPS_EVALUE_LOG_WEIBULL | HICOPS_EVALUE_SMOOTH)) {
+        set_error("unknown evalue_mode bits");
+        return HICOPS_EINVAL;
+    }
     if (p->intensity_scale < 1) { set_error("intensity_scale must be >= 1"); return HICOPS_EINVAL; }
     if (p->min_shared < 1) { set_error("min_shared must be >= 1"); return HICOPS_EINVAL; }
     // a peptide shares at most one ion per query bin

@@ -232,7 +232,7 @@ hicops_status enqueue_search(hicops_index* idx, const DevBatch& d, uint32_t n, c
     st = launch_search(sa, cfg, (uint64_t)n * max_seg, s);
     if (st != HICOPS_OK) return st;
     mark(idx, 3, s, timing_marks);
-    MergeArgs ma{w.seg_off, w.utop, d_hist, n, k, 0, d_psm, idx->pid_stride, idx->pid_base};
+    MergeArgs ma{w.seg_off, w.utop, d_hist, n, k, 0, d_psm, idx->pid_stride, idx->pid_base, p.evalue_mode};
     merge_kernel<<<(n + kMergeWarps - 1) / kMergeWarps, kMergeWarps * 32, 0, s>>>(ma);
     count_launches(1);
     HC_CUDA(cudaGetLastError());
@@ -698,15 +698,19 @@ __global__ void shard_gather_kernel(const hicops_psm* __restrict__ parts, uint32
 
 extern "C" hicops_status hicops_merge_shards(uint32_t n_shards, uint32_t n, uint32_t top_k,
                                              const hicops_psm* shard_psm, const uint32_t* hist,
-                                             const uint32_t* nscored, uint32_t hist_parts, int on_device,
-                                             void* cuda_stream, hicops_psm* out_psm, uint32_t* out_hist,
-                                             uint32_t* out_nscored) {
+                                             const uint32_t* nscored, uint32_t hist_parts,
+                                             uint32_t evalue_mode, int on_device, void* cuda_stream,
+                                             hicops_psm* out_psm, uint32_t* out_hist, uint32_t* out_nscored) {
     if (n_shards < 1 || n_shards > HICOPS_MAX_SHARDS) {
         set_error("n_shards must be in [1, %u]", (unsigned)HICOPS_MAX_SHARDS);
         return HICOPS_EINVAL;
     }
     if (top_k < 1 || top_k > kMaxTopK) { set_error("top_k must be in [1, %u]", kMaxTopK); return HICOPS_EINVAL; }
     if (hist_parts != 1 && hist_parts != n_shards) { set_error("hist_parts must be 1 or n_shards"); return HICOPS_EINVAL; }
+    if (evalue_mode & ~(HICOPS_EVALUE_LOG_WEIBULL | HICOPS_EVALUE_SMOOTH)) {
+        set_error("unknown evalue_mode bits");
+        return HICOPS_EINVAL;
+    }
     if (n == 0) return HICOPS_OK;
     if (!shard_psm || !hist || !nscored || !out_psm) { set_error("NULL argument"); return HICOPS_EINVAL; }
     cudaStream_t s = (cudaStream_t)cuda_stream;
@@ -741,7 +745,7 @@ extern "C" hicops_status hicops_merge_shards(uint32_t n_shards, uint32_t n, uint
                                               seg_off, d_hist, d_ns);
         count_launches(1);
         HC_CUDA(cudaGetLastError());
-        MergeArgs ma{seg_off, utop, d_hist, n, top_k, 0, d_out, 1u, 0u};
+        MergeArgs ma{seg_off, utop, d_hist, n, top_k, 0, d_out, 1u, 0u, evalue_mode};
         merge_kernel<<<(n + kMergeWarps - 1) / kMergeWarps, kMergeWarps * 32, 0, s>>>(ma);
         count_launches(1);
         HC_CUDA(cudaGetLastError());

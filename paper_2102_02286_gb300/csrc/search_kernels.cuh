@@ -287,6 +287,7 @@ struct MergeArgs {
     uint32_t q_base;          // query index written into the rows
     hicops_psm* out;
     uint32_t pid_stride, pid_base;   // row pid = list pid * pid_stride + pid_base
+    uint32_t ev_mode;                // HICOPS_EVALUE_* bits
 };
 
 __device__ __forceinline__ double warp_sum_f64(double v) {
@@ -340,54 +341,102 @@ __global__ void __launch_bounds__(kMergeWarps * 32) merge_kernel(MergeArgs a) {
         if (wp != 0xffffffffu && lane == wl) { if (which == 0) ++h0; else ++h1; }
         if ((uint32_t)lane == r) { row.key = wk; row.pid = wp; row.packed = wpk; }
     }
-    // survival function of the histogram: suf[j] = sum of hist[i >= j]
+    // the histogram, bins 8 lane .. 8 lane + 7 of this lane
     const uint32_t* hq = a.hist + (uint64_t)q * kHistBins + 8 * lane;   // caller's buffer: 4-byte aligned only
     uint32_t v[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) v[i] = hq[i];
-    uint32_t loc[8];
-    uint32_t run = 0;
+    uint32_t nl = 0;
 #pragma unroll
-    for (int i = 7; i >= 0; --i) { run += v[i]; loc[i] = run; }
-    uint32_t above = run;   // inclusive suffix over lanes >= lane
+    for (int i = 0; i < 8; ++i) nl += v[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nl += __shfl_xor_sync(0xffffffffu, nl, o);
+    const double N = (double)nl;
+    // the distribution the fit sees (R16): the histogram, or 35 times its
+    // 5-point quadratic Savitzky-Golay smoothing (zero outside the bins);
+    // integers, so every sum and comparison below is exact
+    int64_t g[8];
+    {
+        const uint32_t l2 = __shfl_up_sync(0xffffffffu, v[6], 1), l1 = __shfl_up_sync(0xffffffffu, v[7], 1);
+        const uint32_t r1 = __shfl_down_sync(0xffffffffu, v[0], 1), r2 = __shfl_down_sync(0xffffffffu, v[1], 1);
+        int64_t e[12];
+        e[0] = lane > 0 ? l2 : 0;
+        e[1] = lane > 0 ? l1 : 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) e[2 + i] = v[i];
+        e[10] = lane < 31 ? r1 : 0;
+        e[11] = lane < 31 ? r2 : 0;
+        const bool smooth = (a.ev_mode & HICOPS_EVALUE_SMOOTH) != 0u;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            g[i] = smooth ? -3 * e[i] + 12 * e[i + 1] + 17 * e[i + 2] + 12 * e[i + 3] - 3 * e[i + 4] : e[i + 2];
+    }
+    // survival G[j] = sum of g[i >= j]: within the lane, then over the lanes above
+    int64_t loc[8];
+    int64_t run = 0;
+#pragma unroll
+    for (int i = 7; i >= 0; --i) { run += g[i]; loc[i] = run; }
+    int64_t above = run;   // inclusive suffix over lanes >= lane
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_down_sync(0xffffffffu, above, o);
+        const int64_t y = __shfl_down_sync(0xffffffffu, above, o);
         if (lane + o < 32) above += y;
     }
-    const double N = (double)__shfl_sync(0xffffffffu, above, 0);
+    const int64_t G0 = __shfl_sync(0xffffffffu, above, 0);
     above -= run;           // lanes > lane
-    // mode: the highest count, the lowest bin on ties
-    uint64_t best = 0;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const uint64_t c = ((uint64_t)v[i] << 32) | (uint32_t)(255 - (8 * lane + i));
-        if (c > best) best = c;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const uint64_t ob = __shfl_xor_sync(0xffffffffu, best, o);
-        if (ob > best) best = ob;
-    }
-    const int mode = 255 - (int)(best & 0xffffffffu);
+    const double dG0 = (double)G0;
     const int64_t key0 = __shfl_sync(0xffffffffu, row.key, 0);
     const uint32_t pid0 = __shfl_sync(0xffffffffu, row.pid, 0);
     const bool have_top = pid0 != 0xffffffffu;
-    int64_t jtop = 0;
-    if (have_top) { jtop = key0 >> 31; if (jtop > 255) jtop = 255; }
+    const bool weibull = (a.ev_mode & HICOPS_EVALUE_LOG_WEIBULL) != 0u;
     double cn = 0, sx = 0, sy = 0, sxx = 0, sxy = 0;
+    if (weibull) {
+        // R17: least squares of -ln(-ln F_j) on x = j + 1, F_j = 1 - G[j+1] / G[0],
+        // over the bins with 0 < F_j < 1
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int j = 8 * lane + i;
-        const uint32_t sj = loc[i] + above;
-        if (have_top && j >= mode + 1 && j <= jtop - 1 && sj > 0) {
-            const double x = (double)j;
-            const double y = log10((double)sj / N);
-            cn += 1.0;
-            sx += x;
-            sy += y;
-            sxx += x * x;
-            sxy += x * y;
+        for (int i = 0; i < 8; ++i) {
+            const int j = 8 * lane + i;
+            const int64_t gn = loc[i] + above - g[i];   // G[j + 1]
+            if (have_top && gn > 0 && gn < G0) {
+                const double x = (double)(j + 1);
+                const double y = -log(-log1p(-((double)gn / dG0)));
+                cn += 1.0;
+                sx += x;
+                sy += y;
+                sxx += x * x;
+                sxy += x * y;
+            }
+        }
+    } else {
+        // R12 on g: the mode (largest g, lowest bin on ties), then the line
+        // through (j, log10(G[j] / G[0])) for j in [mode + 1, jtop - 1], G[j] > 0
+        int64_t bv = g[0];
+        int bj = 8 * lane;
+#pragma unroll
+        for (int i = 1; i < 8; ++i)
+            if (g[i] > bv) { bv = g[i]; bj = 8 * lane + i; }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const int64_t ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+            if (ov > bv || (ov == bv && oj < bj)) { bv = ov; bj = oj; }
+        }
+        const int mode = bj;
+        int64_t jtop = 0;
+        if (have_top) { jtop = key0 >> 31; if (jtop > 255) jtop = 255; }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int j = 8 * lane + i;
+            const int64_t gj = loc[i] + above;   // G[j]
+            if (have_top && j >= mode + 1 && j <= jtop - 1 && gj > 0) {
+                const double x = (double)j;
+                const double y = log10((double)gj / dG0);
+                cn += 1.0;
+                sx += x;
+                sy += y;
+                sxx += x * x;
+                sxy += x * y;
+            }
         }
     }
     cn = warp_sum_f64(cn);
@@ -395,12 +444,13 @@ __global__ void __launch_bounds__(kMergeWarps * 32) merge_kernel(MergeArgs a) {
     sy = warp_sum_f64(sy);
     sxx = warp_sum_f64(sxx);
     sxy = warp_sum_f64(sxy);
-    const bool fit = cn >= 3.0;
+    bool fit = cn >= 3.0;
     double wfit = 0.0, bfit = 0.0;
     if (fit) {
         const double den = cn * sxx - sx * sx;
         wfit = (cn * sxy - sx * sy) / den;
         bfit = (sy - wfit * sx) / cn;
+        if (weibull) fit = wfit > 0.0;
     }
     if ((uint32_t)lane < k) {
         hicops_psm o;
@@ -412,7 +462,10 @@ __global__ void __launch_bounds__(kMergeWarps * 32) merge_kernel(MergeArgs a) {
             o.ny = (uint8_t)((row.packed >> kNyShift) & 63u);
             o.key = row.key;
             o.hyperscore = (float)((double)row.key * 0x1p-32);
-            o.evalue = fit ? N * exp10(wfit * ((double)row.key * 0x1p-31) + bfit) : N;
+            const double x = (double)row.key * 0x1p-31;
+            if (!fit) o.evalue = N;
+            else if (weibull) o.evalue = N * -expm1(-exp(-(wfit * x + bfit)));   // N * P(score >= x)
+            else o.evalue = N * exp10(wfit * x + bfit);
         } else {
             o.pid = 0xffffffffu;
             o.nb = o.ny = 0;

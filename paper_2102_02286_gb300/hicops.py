@@ -38,7 +38,8 @@ class Params(C.Structure):
                 ("max_total_mods", C.c_uint32), ("min_mass", C.c_double), ("max_mass", C.c_double),
                 ("frag_mz_min", C.c_double), ("frag_mz_max", C.c_double), ("bin_width_da", C.c_double),
                 ("top_n_peaks", C.c_uint32), ("min_shared", C.c_uint32), ("top_k", C.c_uint32),
-                ("hist_bins", C.c_uint32), ("intensity_scale", C.c_uint32), ("tol_bins", C.c_uint32)]
+                ("hist_bins", C.c_uint32), ("intensity_scale", C.c_uint32), ("tol_bins", C.c_uint32),
+                ("evalue_mode", C.c_uint32), ("reserved", C.c_uint32)]
 
 
 class Proteins(C.Structure):
@@ -131,7 +132,8 @@ def load(build_if_missing: bool = False):
         "hicops_kernel_launches": (C.c_uint64, []),
         "hicops_index_get_stats": (st, [P, C.POINTER(IndexStats)]),
         "hicops_index_shard": (st, [P, C.c_uint32, C.c_uint32, C.POINTER(P)]),
-        "hicops_merge_shards": (st, [C.c_uint32, C.c_uint32, C.c_uint32, P, P, P, C.c_uint32, C.c_int, P, P, P, P]),
+        "hicops_merge_shards": (st, [C.c_uint32, C.c_uint32, C.c_uint32, P, P, P, C.c_uint32, C.c_uint32, C.c_int,
+                                     P, P, P, P]),
         "hicops_peptide": (st, [P, C.c_uint32, C.c_char_p, C.c_uint32, P, P]),
         "hicops_index_copy_csr": (st, [P, P, P]),
         "hicops_index_free": (None, [P]),
@@ -159,7 +161,8 @@ def make_params(sp) -> Params:
                   max_total_mods=sp.max_total_mods, min_mass=sp.min_mass, max_mass=sp.max_mass,
                   frag_mz_min=sp.frag_mz_min, frag_mz_max=sp.frag_mz_max, bin_width_da=sp.bin_width_da,
                   top_n_peaks=sp.top_n_peaks, min_shared=sp.min_shared, top_k=sp.top_k,
-                  hist_bins=sp.hist_bins, intensity_scale=sp.intensity_scale, tol_bins=sp.tol_bins)
+                  hist_bins=sp.hist_bins, intensity_scale=sp.intensity_scale, tol_bins=sp.tol_bins,
+                  evalue_mode=sp.evalue_mode, reserved=0)
 
 
 @dataclass
@@ -450,7 +453,7 @@ class Server:
 
 
 def merge_shards(n_shards: int, n: int, top_k: int, psm, hist, n_scored, hist_parts: int,
-                 stream=None) -> "DeviceResult":
+                 stream=None, evalue_mode: int = 0) -> "DeviceResult":
     """hicops_merge_shards on device tensors (asynchronous on the stream):
     psm [n_shards * n * top_k] rows, hist [hist_parts * n * 256], n_scored
     [hist_parts * n]; returns a DeviceResult of the merged search."""
@@ -458,19 +461,19 @@ def merge_shards(n_shards: int, n: int, top_k: int, psm, hist, n_scored, hist_pa
     s = stream if stream is not None else torch.cuda.current_stream()
     out = DeviceResult.alloc(n, top_k)
     _check(load().hicops_merge_shards(n_shards, n, top_k, psm.data_ptr(), hist.data_ptr(), n_scored.data_ptr(),
-                                      hist_parts, 1, s.cuda_stream, out.psm.data_ptr(), out.hist.data_ptr(),
-                                      out.n_scored.data_ptr()))
+                                      hist_parts, evalue_mode, 1, s.cuda_stream, out.psm.data_ptr(),
+                                      out.hist.data_ptr(), out.n_scored.data_ptr()))
     return out
 
 
 def merge_shards_host(n_shards: int, n: int, top_k: int, psm: np.ndarray, hist: np.ndarray,
-                      n_scored: np.ndarray, hist_parts: int) -> SearchResult:
+                      n_scored: np.ndarray, hist_parts: int, evalue_mode: int = 0) -> SearchResult:
     """hicops_merge_shards on host arrays (the library copies to the device and back)."""
     psm = np.ascontiguousarray(psm, PSM_DTYPE)
     hist = np.ascontiguousarray(hist, np.uint32)
     n_scored = np.ascontiguousarray(n_scored, np.uint32)
     out = SearchResult(np.zeros((n, top_k), PSM_DTYPE), np.zeros((n, HIST_BINS), np.uint32),
                        np.zeros(n, np.uint32))
-    _check(load().hicops_merge_shards(n_shards, n, top_k, _ptr(psm), _ptr(hist), _ptr(n_scored), hist_parts, 0,
-                                      None, _ptr(out.psm), _ptr(out.hist), _ptr(out.n_scored)))
+    _check(load().hicops_merge_shards(n_shards, n, top_k, _ptr(psm), _ptr(hist), _ptr(n_scored), hist_parts,
+                                      evalue_mode, 0, None, _ptr(out.psm), _ptr(out.hist), _ptr(out.n_scored)))
     return out

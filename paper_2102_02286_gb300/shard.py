@@ -80,7 +80,7 @@ def sharded_search(shard_index: hc.Index, dev_batch: hc.DeviceBatch, store, step
     torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
     publish_and_wait(store, step, rank, world, timeout_s)
     rows, hist, ns = exchange(part.psm, part.hist, part.n_scored, group)
-    return hc.merge_shards(world, n, k, rows, hist, ns, 1, stream)
+    return hc.merge_shards(world, n, k, rows, hist, ns, 1, stream, shard_index.params.evalue_mode)
 
 
 def local_sharded_search(shards: List[hc.Index], dev_batch: hc.DeviceBatch,
@@ -96,4 +96,4 @@ def local_sharded_search(shards: List[hc.Index], dev_batch: hc.DeviceBatch,
     rows = torch.cat([p.psm for p in parts])
     hist = torch.cat([p.hist for p in parts])
     ns = torch.cat([p.n_scored for p in parts])
-    return hc.merge_shards(P, n, k, rows, hist, ns, P, stream)
+    return hc.merge_shards(P, n, k, rows, hist, ns, P, stream, shards[0].params.evalue_mode)
