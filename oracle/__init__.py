@@ -79,6 +79,11 @@ def lib():
         L.or_evalue.argtypes = [P, C.c_uint32, P, P, C.c_uint32, C.c_uint32, P]
         L.or_search.argtypes = [P, P, P, P, P, P, P, P, C.c_uint32, P, P, P, P, P]
         L.or_search_shard.argtypes = [P, P, P, P, P, P, P, P, C.c_uint32, P, P, P, P, P, C.c_uint32, C.c_uint32]
+        L.or_edit_distance.restype = C.c_uint32
+        L.or_edit_distance.argtypes = [C.c_char_p, P, C.c_char_p, P]
+        L.or_mod_distance.restype = C.c_double
+        L.or_mod_distance.argtypes = [C.c_char_p, P, C.c_char_p, P]
+        L.or_partition_lbe.argtypes = [P, C.c_uint32, P]
     return _lib
 
 
@@ -148,6 +153,12 @@ class OracleDb:
         n = lib().or_db_ions(self.h, pid, _ptr(b), _ptr(y))
         return b[:n].copy(), y[:n].copy()
 
+    def partition_lbe(self, n_parts: int) -> np.ndarray:
+        """R18: the LBE partition of the database, part[pid] in [0, n_parts)."""
+        out = np.zeros(self.n, np.uint32)
+        lib().or_partition_lbe(self.h, n_parts, _ptr(out))
+        return out
+
     def bins(self, pid: int):
         b = np.zeros(256, np.uint32)
         t = np.zeros(256, np.uint8)
@@ -201,3 +212,27 @@ def evalue(hist, keys, pids, evalue_mode=0) -> np.ndarray:
     out = np.zeros(len(keys), np.float64)
     lib().or_evalue(_ptr(hist), len(hist), _ptr(keys), _ptr(pids), len(keys), evalue_mode, _ptr(out))
     return out
+
+
+def _seq_codes(pep):
+    """(letters, codes) from a peptide written with '*' after modified residues."""
+    letters, codes = [], []
+    for ch in pep:
+        if ch == "*":
+            codes[-1] = 1
+        else:
+            letters.append(ch)
+            codes.append(0)
+    return "".join(letters).encode(), np.array(codes, np.uint8)
+
+
+def edit_distance(x: str, y: str) -> int:
+    """R18 edit distance of two peptides written with '*' after modified residues."""
+    (xs, xc), (ys, yc) = _seq_codes(x), _seq_codes(y)
+    return int(lib().or_edit_distance(xs, _ptr(xc), ys, _ptr(yc)))
+
+
+def mod_distance(x: str, y: str) -> float:
+    """R18 Mod Distance of two peptides written with '*' after modified residues."""
+    (xs, xc), (ys, yc) = _seq_codes(x), _seq_codes(y)
+    return float(lib().or_mod_distance(xs, _ptr(xc), ys, _ptr(yc)))

@@ -55,6 +55,15 @@
 //   R16 (optional) the fit sees the histogram smoothed by the 5-point
 //      quadratic Savitzky-Golay filter (taps -3 12 17 12 -3 over 35, zero
 //      outside the bins), kept as 35 times its value so it stays integer;
+//   R18 LBE partition with the Mod Distance: a cluster is the set of entries
+//      sharing one unmodified sequence; inside a cluster entries are ordered
+//      by (edit distance to the unmodified sequence, Mod Distance to it,
+//      pid); clusters follow one another in the order of their smallest
+//      pid; position i of that sequence goes to partition i mod P.  Edit
+//      distance: Levenshtein over residues, a modified residue being a
+//      symbol of its own; Mod Distance 2 - a / max(len x, len y), a = the
+//      letters equal from the N-terminus up to the first edit plus those
+//      equal from the C-terminus up to the last edit (2 len when x = y);
 //   R17 (optional, instead of R12) log-Weibull (Gumbel) fit: least squares
 //      of -ln(-ln F_j) on x = j + 1, F_j = fraction scoring below j + 1, over
 //      bins with 0 < F_j < 1; e = N * (1 - exp(-exp(-(a x + c)))), x =
@@ -368,9 +377,85 @@ void evalues(const uint32_t* hist, uint32_t nbins, const std::vector<OrPsm>& top
     }
 }
 
+// R18: residue i of a peptide as one symbol (letter, modification code)
+uint32_t symbol(const std::string& seq, const std::vector<uint8_t>& code, size_t i) {
+    return (uint32_t)(unsigned char)seq[i] << 8 | code[i];
+}
+
+// R18: Levenshtein distance (unit insertions, deletions, substitutions)
+uint32_t edit_distance(const std::string& xs, const std::vector<uint8_t>& xc, const std::string& ys,
+                       const std::vector<uint8_t>& yc) {
+    const size_t n = xs.size(), m = ys.size();
+    std::vector<uint32_t> prev(m + 1), cur(m + 1);
+    for (size_t j = 0; j <= m; ++j) prev[j] = (uint32_t)j;
+    for (size_t i = 1; i <= n; ++i) {
+        cur[0] = (uint32_t)i;
+        for (size_t j = 1; j <= m; ++j) {
+            const uint32_t sub = prev[j - 1] + (symbol(xs, xc, i - 1) == symbol(ys, yc, j - 1) ? 0u : 1u);
+            cur[j] = std::min({prev[j] + 1u, cur[j - 1] + 1u, sub});
+        }
+        std::swap(prev, cur);
+    }
+    return prev[m];
+}
+
+// R18: Mod Distance 2 - a / max(len x, len y)
+double mod_distance(const std::string& xs, const std::vector<uint8_t>& xc, const std::string& ys,
+                    const std::vector<uint8_t>& yc) {
+    const size_t n = xs.size(), m = ys.size();
+    size_t a = 0;
+    for (size_t i = 0; i < std::min(n, m) && symbol(xs, xc, i) == symbol(ys, yc, i); ++i) ++a;   // from the N-terminus
+    for (size_t i = 0; i < std::min(n, m) && symbol(xs, xc, n - 1 - i) == symbol(ys, yc, m - 1 - i); ++i) ++a;   // C
+    return 2.0 - (double)a / (double)std::max(n, m);
+}
+
 }  // namespace
 
 extern "C" {
+
+// R18 for two peptides given as letters and per-position modification codes
+// (0 = none): edit distance and Mod Distance.
+uint32_t or_edit_distance(const char* x, const uint8_t* xc, const char* y, const uint8_t* yc) {
+    const std::string xs(x), ys(y);
+    return edit_distance(xs, std::vector<uint8_t>(xc, xc + xs.size()), ys, std::vector<uint8_t>(yc, yc + ys.size()));
+}
+
+double or_mod_distance(const char* x, const uint8_t* xc, const char* y, const uint8_t* yc) {
+    const std::string xs(x), ys(y);
+    return mod_distance(xs, std::vector<uint8_t>(xc, xc + xs.size()), ys, std::vector<uint8_t>(yc, yc + ys.size()));
+}
+
+// R18: the LBE partition of the database over n_parts: part[pid].
+void or_partition_lbe(void* h, uint32_t n_parts, uint32_t* part) {
+    const Db* db = (Db*)h;
+    const size_t P = db->peps.size();
+    std::map<std::string, std::vector<uint32_t>> clusters;   // unmodified sequence -> pids (ascending)
+    for (size_t pid = 0; pid < P; ++pid) clusters[db->peps[pid].seq].push_back((uint32_t)pid);
+    std::vector<std::vector<uint32_t>> order;
+    for (auto& kv : clusters) {
+        const std::string& base = kv.first;
+        const std::vector<uint8_t> none(base.size(), 0);
+        std::vector<uint32_t> c = kv.second;
+        std::stable_sort(c.begin(), c.end(), [&](uint32_t x, uint32_t y) {
+            const Peptide& px = db->peps[x];
+            const Peptide& py = db->peps[y];
+            const uint32_t ex = edit_distance(px.seq, px.code, base, none);
+            const uint32_t ey = edit_distance(py.seq, py.code, base, none);
+            if (ex != ey) return ex < ey;
+            const double mx = mod_distance(px.seq, px.code, base, none);
+            const double my = mod_distance(py.seq, py.code, base, none);
+            if (mx != my) return mx < my;
+            return x < y;
+        });
+        order.push_back(c);
+    }
+    std::sort(order.begin(), order.end(), [&](const std::vector<uint32_t>& x, const std::vector<uint32_t>& y) {
+        return *std::min_element(x.begin(), x.end()) < *std::min_element(y.begin(), y.end());
+    });
+    size_t i = 0;
+    for (auto& c : order)
+        for (uint32_t pid : c) part[pid] = (uint32_t)(i++ % n_parts);
+}
 
 // Builds the oracle's peptide database (Superstep 1 without an index).
 void* or_db_build(const char* seq, const uint64_t* prot_off, uint32_t n_prot,

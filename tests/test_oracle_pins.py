@@ -18,6 +18,9 @@
   fit (R17) against numpy's polyfit and scipy's Gumbel survival function,
   and the recovery of a known Gumbel's location and scale from its binned
   counts;
+* the LBE partition (R18): the paper's Mod Distance worked example, textbook
+  edit distances, a Python brute force of the partition, and its balance
+  (partition sizes and every cluster split evenly);
 * the fragment tolerance of t bins (R15): a hand-worked spectrum with peaks
   one and two bins off the ions and two peaks covering one ion, the brute
   force above with every (ion, peak) pair compared by bin distance, the
@@ -695,3 +698,72 @@ def test_evalue_variant_fallbacks(oracle_lib):
         assert oracle_lib.evalue(h, _keys([30.2]), np.zeros(1, np.uint32), mode)[0] == 77.0
         e = oracle_lib.evalue(h, np.array([np.iinfo(np.int64).min], np.int64), np.array([0xFFFFFFFF], np.uint32), mode)
         assert np.isinf(e[0])
+
+
+# ---------------------------------------------------------------- R18: LBE
+
+
+def test_mod_distance_worked_example(oracle_lib):
+    with open(os.path.join(GOLDEN, "mod_distance_example.txt")) as f:
+        rows = [l.split() for l in f if l.strip() and not l.startswith("#")]
+    assert len(rows) == 2
+    for x, y, de, dm in rows:
+        assert oracle_lib.edit_distance(x, y) == int(de)
+        assert oracle_lib.mod_distance(x, y) == float(dm)
+        assert oracle_lib.mod_distance(y, x) == float(dm)
+
+
+def test_edit_distance_textbook(oracle_lib):
+    assert oracle_lib.edit_distance("KITTEN", "SITTING") == 3
+    assert oracle_lib.edit_distance("FLAW", "LAWN") == 2
+    assert oracle_lib.edit_distance("PEPTIDE", "PEPTIDE") == 0
+    assert oracle_lib.edit_distance("PEPTIDE", "PEPTIDEK") == 1
+    assert oracle_lib.edit_distance("A", "A*") == 1            # a modified residue is another symbol
+    assert oracle_lib.edit_distance("M*M*", "MM") == 2
+    assert oracle_lib.mod_distance("PEPTIDE", "PEPTIDE") == 0.0
+    assert oracle_lib.mod_distance("PEPTIDE", "P*EPTIDE") == 2 - 6 / 7
+
+
+def _py_levenshtein(a, b):
+    d = [[i + j if i * j == 0 else 0 for j in range(len(b) + 1)] for i in range(len(a) + 1)]
+    for i in range(1, len(a) + 1):
+        for j in range(1, len(b) + 1):
+            d[i][j] = min(d[i - 1][j] + 1, d[i][j - 1] + 1, d[i - 1][j - 1] + (a[i - 1] != b[j - 1]))
+    return d[len(a)][len(b)]
+
+
+def test_lbe_partition_brute_force_and_balance(oracle_lib):
+    w = configs.OPEN_MEDIUM.with_proteins(25)
+    prot = synth.make_proteome(w.n_proteins, w.db_seed, w.protein_len)
+    db = oracle_lib.OracleDb(prot.seq, prot.off, w.mods, w.params)
+    peps = [db.peptide(i) for i in range(db.n)]
+    clusters = {}
+    for pid, (seq, _, codes) in enumerate(peps):
+        clusters.setdefault(seq, []).append(pid)
+    order = []
+    for seq, members in sorted(clusters.items(), key=lambda kv: min(kv[1])):
+        base = [(c, 0) for c in seq]
+
+        def key(pid):
+            sym = list(zip(peps[pid][0], (int(c) for c in peps[pid][2])))
+            a = 0
+            while a < len(sym) and sym[a] == base[a]:
+                a += 1
+            b = 0
+            while b < len(sym) and sym[-1 - b] == base[-1 - b]:
+                b += 1
+            return (_py_levenshtein(sym, base), 2 - (a + b) / len(sym), pid)
+
+        order.extend(sorted(members, key=key))
+    assert sorted(order) == list(range(db.n))
+    assert any(len(m) > 3 for m in clusters.values())
+    for n_parts in (1, 3, 8):
+        part = db.partition_lbe(n_parts)
+        want = np.zeros(db.n, np.uint32)
+        want[np.array(order)] = np.arange(db.n) % n_parts
+        np.testing.assert_array_equal(part, want)
+        sizes = np.bincount(part, minlength=n_parts)
+        assert sizes.max() - sizes.min() <= 1
+        for members in clusters.values():
+            per = np.bincount(part[members], minlength=n_parts)
+            assert per.max() - per.min() <= 1 or len(members) < n_parts
