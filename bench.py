@@ -49,10 +49,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--tune-spectra", type=int, default=20000, help="autotuner sample (0 = default shape)")
-    ap.add_argument("--mode", default="step", choices=["step", "batched", "serving"],
+    ap.add_argument("--mode", default="step", choices=["step", "batched", "serving", "shards"],
                     help="step: the headline search step; batched: one autotuned graph-replayed launch over "
                          "an uneven batch against plain per-class launches; serving: Poisson request stream "
-                         "through the continuous-batching server against a one-batch-per-launch loop")
+                         "through the continuous-batching server against a one-batch-per-launch loop; shards: "
+                         "per-part work and search time of an n-way database partition (LBE, round-robin, "
+                         "contiguous mass ranges) and the exactness of the merge")
+    ap.add_argument("--parts", type=int, default=8, help="shards: number of database parts")
     ap.add_argument("--loads", default="10000,30000,100000,300000,1000000,2000000",
                     help="serving: offered loads in spectra/s")
     ap.add_argument("--load-seconds", type=float, default=3.0, help="serving: arrival window per load")
@@ -458,6 +461,84 @@ def run_serving(args):
     return 0 if identical else 1
 
 
+def run_shards(args):
+    """Load balance of a database partition (Superstep 1's LBE with the Mod
+    Distance): the database split into --parts parts three ways, each part
+    searched alone over the same batch on this GPU; per part the index
+    entries inside the windows (the search's work) and the search kernel's
+    time (CUDA events, median of --steps after --warmup), their coefficient
+    of variation and max / mean; the parts' merge must equal the unsharded
+    search."""
+    import torch
+    from paper_2102_02286_gb300 import build as pkg_build
+    from paper_2102_02286_gb300 import hicops as hc
+    from paper_2102_02286_gb300 import shard
+
+    torch.cuda.set_device(0)
+    pkg_build.build()
+    hc.load()
+    w = workload(args)
+    if not args.spectra:
+        w = w.with_spectra(min(w.spectra.n_spectra, 20000))
+    prot = synth.make_proteome(w.n_proteins, w.db_seed, w.protein_len)
+    spec = synth.make_spectra(prot, w)
+    idx = hc.Index(prot.seq, prot.off, w.mods, w.params)
+    n, k, P = spec.n, w.params.top_k, args.parts
+    db = hc.DeviceBatch.from_spectra(spec)
+    ref = idx.search(spec)
+    n_pep = idx.stats().n_peptides
+    cuts = np.linspace(0, n_pep, P + 1).astype(np.int64)
+    t0 = time.perf_counter()
+    part = idx.partition_lbe(P)
+    t_lbe = time.perf_counter() - t0
+    makers = {
+        "lbe": lambda: [idx.subset(np.flatnonzero(part == s).astype(np.uint32)) for s in range(P)],
+        "round_robin": lambda: [idx.shard(P, s) for s in range(P)],
+        "contiguous": lambda: [idx.subset(np.arange(cuts[s], cuts[s + 1], dtype=np.uint32)) for s in range(P)],
+    }
+    out = hc.DeviceResult.alloc(n, k)
+    res = {}
+    identical = True
+    for name, make in makers.items():
+        parts = make()
+        work, ms = [], []
+        for p in parts:
+            work.append(float(p.search_work(spec)[3].sum()))
+            p.set_timing(True)
+            for _ in range(args.warmup):
+                p.search_device(db, out)
+            t = []
+            for _ in range(args.steps):
+                p.search_device(db, out)
+                t.append(p.last_timing().search_ms)
+            ms.append(statistics.median(t))
+        merged = shard.local_sharded_search(parts, db).to_host(n, k)
+        same = bool(np.array_equal(merged.psm, ref.psm) and np.array_equal(merged.hist, ref.hist)
+                    and np.array_equal(merged.n_scored, ref.n_scored))
+        identical &= same
+        wv, mv = np.array(work), np.array(ms)
+        res[name] = {"work_cv": float(wv.std() / wv.mean()), "time_cv": float(mv.std() / mv.mean()),
+                     "time_max_over_mean": float(mv.max() / mv.mean()), "search_ms_per_part": [round(x, 3) for x in ms],
+                     "window_entries_per_part": [int(x) for x in work], "identical_results": same}
+        for p in parts:
+            p.close()
+    idx.close()
+    line = {
+        "metric": f"search-time imbalance of a {P}-way LBE database partition (max/mean over parts)",
+        "value": res["lbe"]["time_max_over_mean"],
+        "unit": "ratio",
+        "higher_is_better": False,
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "data": "synthetic",
+        "config": {"workload": workload_desc(w), "spectra": n, "parts": P, "n_peptides": int(n_pep),
+                   "lbe_partition_s": t_lbe},
+        "partitions": res,
+        "identical_results": identical,
+    }
+    print(json.dumps(line), flush=True)
+    return 0 if identical else 1
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -466,6 +547,8 @@ def main():
         return run_batched(args)
     if args.mode == "serving":
         return run_serving(args)
+    if args.mode == "shards":
+        return run_shards(args)
     import torch
     import torch.distributed as dist
     from paper_2102_02286_gb300 import build as pkg_build

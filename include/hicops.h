@@ -248,6 +248,29 @@ hicops_status hicops_index_get_stats(const hicops_index* index, hicops_index_sta
 hicops_status hicops_index_shard(const hicops_index* full, uint32_t n_shards, uint32_t shard,
                                  hicops_index** out);
 
+/* The part of a whole database (hicops_digest; need not be uploaded) holding
+ * the n entries pids[0] < pids[1] < ... (strictly ascending global pids, any
+ * subset: e.g. one partition of hicops_partition_lbe).  Like a shard of
+ * hicops_index_shard it is a host-only index, its rows carry global pids and
+ * hicops_merge_shards combines it with the other parts; it cannot be split
+ * again.  The caller keeps pids.  Errors: HICOPS_EINVAL (NULL, pids not
+ * strictly ascending or not below the database size, index already a part),
+ * HICOPS_ENOMEM. */
+hicops_status hicops_index_subset(const hicops_index* full, const uint32_t* pids, uint64_t n,
+                                  hicops_index** out);
+
+/* The load-balancing partition of Superstep 1 (the improved LBE with the Mod
+ * Distance, Supplementary Text 3 and Supplementary Fig. 3): part[pid] in
+ * [0, n_parts) for every pid of a whole database.  The entries sharing one
+ * unmodified sequence form a cluster, ordered inside by (edit distance to
+ * the unmodified sequence, Mod Distance to it, pid); the clusters follow one
+ * another by their smallest pid and position i of the sequence goes to part
+ * i mod n_parts, so every part holds an equal share (within one entry) of
+ * every cluster and of every mass range.  part [P] is caller-owned host
+ * memory.  Host only.  Errors: HICOPS_EINVAL (NULL, n_parts outside
+ * [1, HICOPS_MAX_SHARDS], index already a part). */
+hicops_status hicops_partition_lbe(const hicops_index* full, uint32_t n_parts, uint32_t* part);
+
 /* Combines the shards' searches of the same n spectra: per spectrum, sums the
  * histograms and candidate counts, merges the shard top-k lists by (key desc,
  * pid asc) and fits the e-value to the summed histogram (the same merge and

@@ -55,6 +55,7 @@ struct DeviceIndex {
     uint32_t skip_stride = 0;      // chunks + 1
     // hot buckets (at least P >> kHotShift entries) as pid bitmaps
     int32_t* hot_id = nullptr;     // [n_bins] (-1 not hot)
+    uint32_t* pid_map = nullptr;   // [P] global pids of a subset (else NULL)
     uint32_t* hot_b = nullptr;     // [n_hot * hot_words] b-ion bits
     uint32_t* hot_y = nullptr;     // [n_hot * hot_words] y-ion bits
     uint32_t* hot_flags = nullptr; // [n_hot] bit 0: has b entries, bit 1: has y entries
@@ -95,6 +96,9 @@ struct hicops_index {
     // a shard of a database holds its entries pid_base, pid_base + pid_stride, ...:
     // global pid = local pid * pid_stride + pid_base (1 and 0 for a whole database)
     uint32_t pid_stride = 1, pid_base = 0;
+    // a subset of a database (hicops_index_subset): global pid of each local
+    // pid, ascending; empty otherwise (then the stride rule holds)
+    std::vector<uint32_t> pid_map;
 
     uint32_t n_bins = 0;           // bins 0 .. n_bins-1 (absolute bin numbers)
     uint64_t s_max = 0;            // largest possible S

@@ -358,18 +358,16 @@ extern "C" hicops_status hicops_index_get_stats(const hicops_index* idx, hicops_
     return HICOPS_OK;
 }
 
-extern "C" hicops_status hicops_index_shard(const hicops_index* full, uint32_t n_shards, uint32_t shard,
-                                            hicops_index** out) {
-    if (!full || !out) { set_error("NULL argument"); return HICOPS_EINVAL; }
-    *out = nullptr;
-    if (full->pid_stride != 1) { set_error("the index is already a shard"); return HICOPS_EINVAL; }
-    if (n_shards < 1 || n_shards > HICOPS_MAX_SHARDS || shard >= n_shards) {
-        set_error("shard %u of %u: need 1 <= n_shards <= %u and shard < n_shards", shard, n_shards,
-                  (unsigned)HICOPS_MAX_SHARDS);
-        return HICOPS_EINVAL;
-    }
+namespace {
+
+bool is_part(const hicops_index* idx) { return idx->pid_stride != 1 || !idx->pid_map.empty(); }
+
+// The part of a whole database holding global pids g(0) < g(1) < ... < g(n-1),
+// as a host-only index (hicops_index_upload builds its device part).
+template <class Global>
+hicops_index* make_part(const hicops_index* full, size_t n, Global g) {
     hicops_index* idx = new (std::nothrow) hicops_index();
-    if (!idx) { set_error("out of host memory"); return HICOPS_ENOMEM; }
+    if (!idx) return nullptr;
     idx->p = full->p;
     memcpy(idx->mres, full->mres, sizeof(idx->mres));
     memcpy(idx->mmod, full->mmod, sizeof(idx->mmod));
@@ -379,37 +377,123 @@ extern "C" hicops_status hicops_index_shard(const hicops_index* full, uint32_t n
     idx->var_max = full->var_max;
     idx->residues = full->residues;
     idx->base_off = full->base_off;
-    const size_t P = full->mass.size();
-    const size_t n = P > shard ? (P - shard + n_shards - 1) / n_shards : 0;
     idx->mass.resize(n);
     idx->base.resize(n);
     idx->mask.resize(n);
-    for (size_t i = 0; i < n; ++i) {   // round-robin over the mass-sorted order
-        const size_t g = i * n_shards + shard;
-        idx->mass[i] = full->mass[g];
-        idx->base[i] = full->base[g];
-        idx->mask[i] = full->mask[g];
+    for (size_t i = 0; i < n; ++i) {
+        const size_t k = g(i);
+        idx->mass[i] = full->mass[k];
+        idx->base[i] = full->base[k];
+        idx->mask[i] = full->mask[k];
     }
-    idx->pid_stride = n_shards;
-    idx->pid_base = shard;
     idx->n_bins = full->n_bins;
     idx->s_max = full->s_max;
     idx->stats = hicops_index_stats{};
     idx->stats.n_peptides = n;
     idx->stats.n_base_peptides = full->stats.n_base_peptides;
     idx->stats.n_bins = full->n_bins;
+    return idx;
+}
+
+}  // namespace
+
+extern "C" hicops_status hicops_index_shard(const hicops_index* full, uint32_t n_shards, uint32_t shard,
+                                            hicops_index** out) {
+    if (!full || !out) { set_error("NULL argument"); return HICOPS_EINVAL; }
+    *out = nullptr;
+    if (is_part(full)) { set_error("the index is already a shard"); return HICOPS_EINVAL; }
+    if (n_shards < 1 || n_shards > HICOPS_MAX_SHARDS || shard >= n_shards) {
+        set_error("shard %u of %u: need 1 <= n_shards <= %u and shard < n_shards", shard, n_shards,
+                  (unsigned)HICOPS_MAX_SHARDS);
+        return HICOPS_EINVAL;
+    }
+    const size_t P = full->mass.size();
+    const size_t n = P > shard ? (P - shard + n_shards - 1) / n_shards : 0;
+    // round-robin over the mass-sorted order
+    hicops_index* idx = make_part(full, n, [&](size_t i) { return i * n_shards + shard; });
+    if (!idx) { set_error("out of host memory"); return HICOPS_ENOMEM; }
+    idx->pid_stride = n_shards;
+    idx->pid_base = shard;
     *out = idx;
+    return HICOPS_OK;
+}
+
+extern "C" hicops_status hicops_index_subset(const hicops_index* full, const uint32_t* pids, uint64_t n,
+                                             hicops_index** out) {
+    if (!full || !out || (n && !pids)) { set_error("NULL argument"); return HICOPS_EINVAL; }
+    *out = nullptr;
+    if (is_part(full)) { set_error("the index is already a shard"); return HICOPS_EINVAL; }
+    const size_t P = full->mass.size();
+    for (uint64_t i = 0; i < n; ++i) {
+        if (pids[i] >= P || (i > 0 && pids[i] <= pids[i - 1])) {
+            set_error("pids must be strictly ascending and below %zu (pids[%llu] = %u)", P,
+                      (unsigned long long)i, pids[i]);
+            return HICOPS_EINVAL;
+        }
+    }
+    hicops_index* idx = make_part(full, n, [&](size_t i) { return (size_t)pids[i]; });
+    if (!idx) { set_error("out of host memory"); return HICOPS_ENOMEM; }
+    idx->pid_map.assign(pids, pids + n);
+    *out = idx;
+    return HICOPS_OK;
+}
+
+// R18, the improved LBE of Superstep 1 (Supplementary Text 3, Supplementary
+// Fig. 3).  Variants of one base peptide differ from it only by modified
+// residues, each a symbol of its own, so their edit distance to it is the
+// number of modified positions, and the letters equal from the termini are
+// the unmodified runs at both ends (the whole peptide, twice, when none is
+// modified); inside a base, a larger run means a smaller Mod Distance.
+extern "C" hicops_status hicops_partition_lbe(const hicops_index* full, uint32_t n_parts, uint32_t* part) {
+    if (!full || !part) { set_error("NULL argument"); return HICOPS_EINVAL; }
+    if (is_part(full)) { set_error("the index is already a shard"); return HICOPS_EINVAL; }
+    if (n_parts < 1 || n_parts > HICOPS_MAX_SHARDS) {
+        set_error("n_parts must be in [1, %u]", (unsigned)HICOPS_MAX_SHARDS);
+        return HICOPS_EINVAL;
+    }
+    const size_t P = full->mass.size();
+    const size_t NB = full->base_off.size() - 1;
+    std::vector<uint32_t> first(NB, UINT32_MAX);   // each cluster's smallest pid
+    for (size_t pid = P; pid-- > 0;) first[full->base[pid]] = (uint32_t)pid;
+    struct Key {
+        uint32_t cluster, edits, ends_rev, pid;   // ends_rev = 2 L - a: ascending = Mod Distance ascending
+    };
+    std::vector<Key> keys(P);
+    parallel_for(P, [&](size_t pid, unsigned) {
+        const uint32_t b = full->base[pid];
+        const uint32_t L = (uint32_t)(full->base_off[b + 1] - full->base_off[b]);
+        const uint64_t m = full->mask[pid];
+        uint32_t a = 2 * L;
+        if (m) a = (uint32_t)__builtin_ctzll(m) + (L - 1 - (63 - (uint32_t)__builtin_clzll(m)));
+        keys[pid] = Key{first[b], (uint32_t)__builtin_popcountll(m), 2 * L - a, (uint32_t)pid};
+    });
+    parallel_sort(keys, [](const Key& x, const Key& y) {
+        if (x.cluster != y.cluster) return x.cluster < y.cluster;
+        if (x.edits != y.edits) return x.edits < y.edits;
+        if (x.ends_rev != y.ends_rev) return x.ends_rev < y.ends_rev;
+        return x.pid < y.pid;
+    });
+    for (size_t i = 0; i < P; ++i) part[keys[i].pid] = (uint32_t)(i % n_parts);
     return HICOPS_OK;
 }
 
 extern "C" hicops_status hicops_peptide(const hicops_index* idx, uint32_t pid, char* seq, uint32_t cap,
                                         double* mass, uint64_t* modmask) {
     if (!idx) { set_error("index is NULL"); return HICOPS_EINVAL; }
-    if (pid < idx->pid_base || (pid - idx->pid_base) % idx->pid_stride != 0) {
-        set_error("pid %u is not in this shard", pid);
-        return HICOPS_EINVAL;
+    if (!idx->pid_map.empty()) {
+        auto it = std::lower_bound(idx->pid_map.begin(), idx->pid_map.end(), pid);
+        if (it == idx->pid_map.end() || *it != pid) {
+            set_error("pid %u is not in this shard", pid);
+            return HICOPS_EINVAL;
+        }
+        pid = (uint32_t)(it - idx->pid_map.begin());
+    } else {
+        if (pid < idx->pid_base || (pid - idx->pid_base) % idx->pid_stride != 0) {
+            set_error("pid %u is not in this shard", pid);
+            return HICOPS_EINVAL;
+        }
+        pid = (pid - idx->pid_base) / idx->pid_stride;
     }
-    pid = (pid - idx->pid_base) / idx->pid_stride;
     if (pid >= idx->mass.size()) { set_error("pid out of range"); return HICOPS_EINVAL; }
     const uint32_t b = idx->base[pid];
     const uint64_t a = idx->base_off[b], e = idx->base_off[b + 1];

@@ -289,6 +289,7 @@ void free_device_index(hicops_index* idx) {
         cudaFree(d.hot_b);
         cudaFree(d.hot_y);
         cudaFree(d.hot_flags);
+        cudaFree(d.pid_map);
         for (void* e : d.ev) if (e) cudaEventDestroy((cudaEvent_t)e);
         if (cur >= 0 && cur != d.device) cudaSetDevice(cur);
     }
@@ -311,6 +312,10 @@ hicops_status upload_index(hicops_index* idx) {
     // persistent parts
     HC_CUDA(cudaMalloc(&d.mass, sizeof(double) * (P ? P : 1)));
     HC_CUDA(cudaMemcpyAsync(d.mass, idx->mass.data(), sizeof(double) * P, cudaMemcpyHostToDevice, s));
+    if (!idx->pid_map.empty()) {   // a subset: its rows report global pids
+        HC_CUDA(cudaMalloc(&d.pid_map, sizeof(uint32_t) * P));
+        HC_CUDA(cudaMemcpyAsync(d.pid_map, idx->pid_map.data(), sizeof(uint32_t) * P, cudaMemcpyHostToDevice, s));
+    }
     HC_CUDA(cudaMalloc(&d.off, sizeof(uint64_t) * (idx->n_bins + 1)));
     // score tables (host libm, FP64): LF[n] = round(2^32 sum_{i<=n} log10 i), LS[s] = round(2^32 log10 s)
     std::vector<int64_t> lf(kMaxLen + 1), ls(idx->s_max + 1);

@@ -232,7 +232,8 @@ hicops_status enqueue_search(hicops_index* idx, const DevBatch& d, uint32_t n, c
     st = launch_search(sa, cfg, (uint64_t)n * max_seg, s);
     if (st != HICOPS_OK) return st;
     mark(idx, 3, s, timing_marks);
-    MergeArgs ma{w.seg_off, w.utop, d_hist, n, k, 0, d_psm, idx->pid_stride, idx->pid_base, p.evalue_mode};
+    MergeArgs ma{w.seg_off, w.utop, d_hist, n, k, 0, d_psm, idx->pid_stride, idx->pid_base, di.pid_map,
+                 p.evalue_mode};
     merge_kernel<<<(n + kMergeWarps - 1) / kMergeWarps, kMergeWarps * 32, 0, s>>>(ma);
     count_launches(1);
     HC_CUDA(cudaGetLastError());
@@ -745,7 +746,7 @@ extern "C" hicops_status hicops_merge_shards(uint32_t n_shards, uint32_t n, uint
                                               seg_off, d_hist, d_ns);
         count_launches(1);
         HC_CUDA(cudaGetLastError());
-        MergeArgs ma{seg_off, utop, d_hist, n, top_k, 0, d_out, 1u, 0u, evalue_mode};
+        MergeArgs ma{seg_off, utop, d_hist, n, top_k, 0, d_out, 1u, 0u, nullptr, evalue_mode};
         merge_kernel<<<(n + kMergeWarps - 1) / kMergeWarps, kMergeWarps * 32, 0, s>>>(ma);
         count_launches(1);
         HC_CUDA(cudaGetLastError());

@@ -286,7 +286,8 @@ struct MergeArgs {
     uint32_t n, k;
     uint32_t q_base;          // query index written into the rows
     hicops_psm* out;
-    uint32_t pid_stride, pid_base;   // row pid = list pid * pid_stride + pid_base
+    uint32_t pid_stride, pid_base;   // row pid = list pid * pid_stride + pid_base ...
+    const uint32_t* pid_map;         // ... or pid_map[list pid] when not NULL
     uint32_t ev_mode;                // HICOPS_EVALUE_* bits
 };
 
@@ -457,7 +458,7 @@ __global__ void __launch_bounds__(kMergeWarps * 32) merge_kernel(MergeArgs a) {
         o.query = a.q_base + q;
         o.reserved = 0;
         if (row.pid != 0xffffffffu) {
-            o.pid = row.pid * a.pid_stride + a.pid_base;
+            o.pid = a.pid_map ? a.pid_map[row.pid] : row.pid * a.pid_stride + a.pid_base;
             o.nb = (uint8_t)(row.packed >> kNbShift);
             o.ny = (uint8_t)((row.packed >> kNyShift) & 63u);
             o.key = row.key;

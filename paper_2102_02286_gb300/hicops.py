@@ -132,6 +132,8 @@ def load(build_if_missing: bool = False):
         "hicops_kernel_launches": (C.c_uint64, []),
         "hicops_index_get_stats": (st, [P, C.POINTER(IndexStats)]),
         "hicops_index_shard": (st, [P, C.c_uint32, C.c_uint32, C.POINTER(P)]),
+        "hicops_index_subset": (st, [P, P, C.c_uint64, C.POINTER(P)]),
+        "hicops_partition_lbe": (st, [P, C.c_uint32, P]),
         "hicops_merge_shards": (st, [C.c_uint32, C.c_uint32, C.c_uint32, P, P, P, C.c_uint32, C.c_uint32, C.c_int,
                                      P, P, P, P]),
         "hicops_peptide": (st, [P, C.c_uint32, C.c_char_p, C.c_uint32, P, P]),
@@ -213,6 +215,23 @@ class Index:
         if upload:
             s.upload()
         return s
+
+    def subset(self, pids, upload: bool = True) -> "Index":
+        """hicops_index_subset: the entries with the given (strictly ascending)
+        global pids; results carry global pids."""
+        pids = np.ascontiguousarray(pids, np.uint32)
+        h = C.c_void_p()
+        _check(load().hicops_index_subset(self.h, _ptr(pids), len(pids), C.byref(h)))
+        s = Index._from_handle(h, self.params)
+        if upload:
+            s.upload()
+        return s
+
+    def partition_lbe(self, n_parts: int) -> np.ndarray:
+        """hicops_partition_lbe: part[pid] of the load-balancing partition."""
+        out = np.zeros(self.stats().n_peptides, np.uint32)
+        _check(load().hicops_partition_lbe(self.h, n_parts, _ptr(out)))
+        return out
 
     def upload(self):
         _check(load().hicops_index_upload(self.h))

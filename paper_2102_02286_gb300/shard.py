@@ -25,6 +25,8 @@ from __future__ import annotations
 import datetime
 from typing import List, Optional
 
+import numpy as np
+
 from . import hicops as hc
 
 
@@ -81,6 +83,13 @@ def sharded_search(shard_index: hc.Index, dev_batch: hc.DeviceBatch, store, step
     publish_and_wait(store, step, rank, world, timeout_s)
     rows, hist, ns = exchange(part.psm, part.hist, part.n_scored, group)
     return hc.merge_shards(world, n, k, rows, hist, ns, 1, stream, shard_index.params.evalue_mode)
+
+
+def lbe_parts(index: hc.Index, n_parts: int, upload: bool = True) -> List[hc.Index]:
+    """The database split by the load-balancing partition (LBE with the Mod
+    Distance, Superstep 1): one subset index per part."""
+    part = index.partition_lbe(n_parts)
+    return [index.subset(np.flatnonzero(part == s).astype(np.uint32), upload) for s in range(n_parts)]
 
 
 def local_sharded_search(shards: List[hc.Index], dev_batch: hc.DeviceBatch,

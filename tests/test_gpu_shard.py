@@ -102,3 +102,28 @@ def test_shard_and_merge_argument_checks(setup):
     with pytest.raises(hc.HicopsError) as e:
         hc.merge_shards_host(2, 3, w.params.top_k, psm, hist, ns, 3)   # hist_parts neither 1 nor 2
     assert e.value.status == hc.EINVAL
+
+
+@pytest.mark.parametrize("n_parts", [3, 8])
+def test_lbe_parts_merge_to_the_unsharded_search_and_balance(setup, n_parts):
+    """The load-balancing partition (LBE with the Mod Distance): its parts
+    merge to the unsharded search bit for bit, and the index entries inside
+    the spectra's windows (the search's work) are spread evenly over the
+    parts, unlike contiguous mass ranges."""
+    from paper_2102_02286_gb300 import shard
+    torch, w, prot, idx, spec, ref = setup
+    parts = shard.lbe_parts(idx, n_parts)
+    P = idx.stats().n_peptides
+    assert sum(p.stats().n_peptides for p in parts) == P
+    out = shard.local_sharded_search(parts, hc.DeviceBatch.from_spectra(spec))
+    torch.cuda.synchronize()
+    _same(out.to_host(spec.n, w.params.top_k), ref)
+    work = np.array([float(p.search_work(spec)[3].sum()) for p in parts])
+    cuts = np.linspace(0, P, n_parts + 1).astype(np.int64)
+    chunks = [idx.subset(np.arange(cuts[s], cuts[s + 1], dtype=np.uint32)) for s in range(n_parts)]
+    cwork = np.array([float(c.search_work(spec)[3].sum()) for c in chunks])
+    assert work.sum() == cwork.sum()
+    cv, ccv = work.std() / work.mean(), cwork.std() / cwork.mean()
+    assert cv < 0.05 and ccv > 4 * cv, (cv, ccv)
+    for s in parts + chunks:
+        s.close()

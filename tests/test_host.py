@@ -109,3 +109,47 @@ def test_digest_global_cap_and_edges(lib, oracle_lib):
     idx = hc.Index(arr, off, mods, p, upload=False)
     db = oracle_lib.OracleDb(arr, off, mods, p)
     _compare_tables(idx, db, mods)
+
+
+# ---------------------------------------------------------------- LBE partition (host only)
+
+
+@pytest.mark.parametrize("name,n_prot,n_parts", [("open_medium", 25, 3), ("open_medium", 40, 8),
+                                                   ("open_large", 10, 5), ("tiny_closed", 60, 4)])
+def test_lbe_partition_matches_oracle(lib, oracle_lib, name, n_prot, n_parts):
+    w = configs.BY_NAME[name].with_proteins(n_prot)
+    prot = synth.make_proteome(w.n_proteins, w.db_seed, w.protein_len)
+    idx = hc.Index(prot.seq, prot.off, w.mods, w.params, upload=False)
+    db = oracle_lib.OracleDb(prot.seq, prot.off, w.mods, w.params)
+    assert idx.stats().n_peptides == db.n
+    np.testing.assert_array_equal(idx.partition_lbe(n_parts), db.partition_lbe(n_parts))
+
+
+def test_subset_indexes(lib):
+    w = configs.OPEN_MEDIUM.with_proteins(20)
+    prot = synth.make_proteome(w.n_proteins, w.db_seed, w.protein_len)
+    idx = hc.Index(prot.seq, prot.off, w.mods, w.params, upload=False)
+    P = idx.stats().n_peptides
+    part = idx.partition_lbe(4)
+    pids = np.flatnonzero(part == 2).astype(np.uint32)
+    sub = idx.subset(pids, upload=False)
+    assert sub.stats().n_peptides == len(pids)
+    for g in pids[::max(1, len(pids) // 20)]:
+        assert sub.peptide(int(g)) == idx.peptide(int(g))   # global pids on the subset
+    other = int(np.flatnonzero(part == 1)[0])
+    with pytest.raises(hc.HicopsError):
+        sub.peptide(other)                                   # not in this part
+    with pytest.raises(hc.HicopsError):
+        sub.subset(pids[:3], upload=False)                   # a part is not split again
+    with pytest.raises(hc.HicopsError):
+        idx.subset(np.array([5, 5, 9], np.uint32), upload=False)   # not strictly ascending
+    with pytest.raises(hc.HicopsError):
+        idx.subset(np.array([1, P], np.uint32), upload=False)      # past the database
+    with pytest.raises(hc.HicopsError):
+        idx.partition_lbe(0)
+    with pytest.raises(hc.HicopsError):
+        sub.partition_lbe(2)
+    empty = idx.subset(np.zeros(0, np.uint32), upload=False)
+    assert empty.stats().n_peptides == 0
+    for h in (sub, empty):
+        h.close()
