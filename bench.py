@@ -49,12 +49,15 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--tune-spectra", type=int, default=20000, help="autotuner sample (0 = default shape)")
-    ap.add_argument("--mode", default="step", choices=["step", "batched", "serving", "shards"],
+    ap.add_argument("--mode", default="step", choices=["step", "batched", "serving", "shards", "ingest"],
                     help="step: the headline search step; batched: one autotuned graph-replayed launch over "
                          "an uneven batch against plain per-class launches; serving: Poisson request stream "
                          "through the continuous-batching server against a one-batch-per-launch loop; shards: "
                          "per-part work and search time of an n-way database partition (LBE, round-robin, "
-                         "contiguous mass ranges) and the exactness of the merge")
+                         "contiguous mass ranges) and the exactness of the merge; ingest: spectra/s from MS2 "
+                         "files through the R/I/K pipeline against the parser alone and the in-memory search")
+    ap.add_argument("--files", type=int, default=8, help="ingest: MS2 files the spectra are written to")
+    ap.add_argument("--workers", type=int, default=0, help="ingest: R + I worker threads (0 = host cores)")
     ap.add_argument("--parts", type=int, default=8, help="shards: number of database parts")
     ap.add_argument("--loads", default="10000,30000,100000,300000,1000000,2000000",
                     help="serving: offered loads in spectra/s")
@@ -539,6 +542,89 @@ def run_shards(args):
     return 0 if identical else 1
 
 
+def run_ingest(args):
+    """The host ingest pipeline (Superstep 3's R/I/K sub-tasks): the
+    workload's spectra written to --files MS2 files, then searched from the
+    files (parse, search, write the rows) by hicops_pipeline_run; the median
+    wall time of --steps runs after --warmup.  Beside it: the parser alone
+    over the same files and one in-memory hicops_search of the same spectra
+    from host buffers.  The rows must equal the in-memory search."""
+    import shutil
+    import tempfile
+
+    import torch
+    from paper_2102_02286_gb300 import build as pkg_build
+    from paper_2102_02286_gb300 import hicops as hc
+
+    torch.cuda.set_device(0)
+    pkg_build.build()
+    hc.load()
+    w = workload(args)
+    if not args.spectra:
+        w = w.with_spectra(min(w.spectra.n_spectra, 20000))
+    prot = synth.make_proteome(w.n_proteins, w.db_seed, w.protein_len)
+    spec = synth.make_spectra(prot, w)
+    tol = float(spec.tol_da[0])
+    if not np.all(spec.tol_da == tol):
+        raise SystemExit("ingest needs a workload with one precursor tolerance")
+    idx = hc.Index(prot.seq, prot.off, w.mods, w.params)
+    n, k = spec.n, w.params.top_k
+    d = tempfile.mkdtemp(prefix="hicops_ingest_")
+    try:
+        cuts = np.linspace(0, n, args.files + 1).astype(np.int64)
+        paths = []
+        for i in range(args.files):
+            p = os.path.join(d, f"part{i}.ms2")
+            synth.write_ms2(spec, p, sel=range(int(cuts[i]), int(cuts[i + 1])))
+            paths.append(p)
+        file_bytes = sum(os.path.getsize(p) for p in paths)
+        workers = args.workers or max(2, os.cpu_count() or 2)
+        out = os.path.join(d, "rows.tsv")
+        runs = []
+        for i in range(args.warmup + args.steps):
+            st = hc.run_files(idx, paths, out, tol, n_workers=workers)
+            if i >= args.warmup:
+                runs.append((st.seconds, st.moves_i_to_r, st.moves_r_to_i, st.wait_seconds, st.batches))
+        secs = statistics.median(r[0] for r in runs)
+        t0 = time.perf_counter()
+        for p in paths:
+            hc.read_ms2(p)
+        parse_s = time.perf_counter() - t0
+        idx.search(spec)
+        t0 = time.perf_counter()
+        ref = idx.search(spec)
+        mem_s = time.perf_counter() - t0
+        rows = hc.read_pipeline_rows(out)
+        q = cuts[:-1][rows["file"]] + rows["spectrum"].astype(np.int64)
+        real = ref.psm["pid"] != 0xFFFFFFFF
+        order = np.lexsort((rows["rank"], q))
+        wq, wr = np.nonzero(real)
+        identical = bool(len(rows) == len(wq) and np.array_equal(q[order], wq)
+                         and np.array_equal(rows["pid"][order], ref.psm["pid"][wq, wr])
+                         and np.array_equal(rows["evalue"][order], ref.psm["evalue"][wq, wr]))
+    finally:
+        shutil.rmtree(d, ignore_errors=True)
+    idx.close()
+    last = runs[-1]
+    line = {
+        "metric": "spectra/s searched from MS2 files through the R/I/K pipeline (parse + search + write)",
+        "value": n / secs,
+        "unit": "spectra/s",
+        "higher_is_better": True,
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "data": "synthetic",
+        "config": {"workload": workload_desc(w), "spectra": n, "files": args.files, "file_bytes": file_bytes,
+                   "workers": workers, "batch_spectra": 4096, "buffers": 20},
+        "seconds_per_run": secs,
+        "parse_only_spectra_per_s": n / parse_s,
+        "in_memory_search_spectra_per_s": n / mem_s,
+        "scheduler": {"moves_i_to_r": last[1], "moves_r_to_i": last[2], "i_wait_s": last[3], "batches": last[4]},
+        "identical_results": identical,
+    }
+    print(json.dumps(line), flush=True)
+    return 0 if identical else 1
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -549,6 +635,8 @@ def main():
         return run_serving(args)
     if args.mode == "shards":
         return run_shards(args)
+    if args.mode == "ingest":
+        return run_ingest(args)
     import torch
     import torch.distributed as dist
     from paper_2102_02286_gb300 import build as pkg_build

@@ -289,6 +289,72 @@ hicops_status hicops_merge_shards(uint32_t n_shards, uint32_t n, uint32_t top_k,
                                   uint32_t evalue_mode, int on_device, void* cuda_stream, hicops_psm* out_psm,
                                   uint32_t* out_hist, uint32_t* out_nscored);
 
+/* ---- host ingest pipeline (Superstep 3's R/I/K sub-tasks: Buffering and
+ * Task Scheduling sections, Supplementary Algorithm 2).  MS2 text files
+ * ("S <scan> <scan> <precursor m/z>", "Z <charge> <[M+H]+>" (the first Z
+ * gives the charge; none = charge 0), optional "H"/"I"/"D" lines, and
+ * "<m/z> <intensity>" peak lines) are parsed into batch buffers by R
+ * workers, searched by I workers (hicops_search on a stream of their own)
+ * and written by one K thread; buffers circulate through a recycle and a
+ * forward queue.  Workers move between R and I by the paper's rules (see
+ * hicops_sched_*), an I worker forecasting its next wait for the forward
+ * queue by double exponential smoothing (hicops_des_step). */
+typedef struct hicops_pipeline_config {
+    uint32_t batch_spectra;   /* spectra per buffer (0 = 4096) */
+    uint32_t n_buffers;       /* buffers in circulation (0 = 20; >= 2) */
+    uint32_t n_workers;       /* R + I worker threads (0 = 4; >= 2); one starts as R */
+    uint32_t reserved;        /* 0 */
+    double prec_tol_da;       /* precursor tolerance dM of every spectrum (>= 0) */
+    double alpha;             /* smoothing factor in (0, 1) (else 0.5) */
+    double t_min_s, t_max_s;  /* wait thresholds t_min and t_max in seconds (<= 0: 1 ms, 50 ms) */
+} hicops_pipeline_config;
+
+typedef struct hicops_pipeline_stats {
+    uint64_t spectra, batches;           /* searched */
+    uint64_t moves_i_to_r, moves_r_to_i; /* scheduler decisions taken */
+    double seconds;                      /* wall time of the run */
+    double wait_seconds;                 /* time I workers waited for the forward queue */
+} hicops_pipeline_stats;
+
+/* Searches every spectrum of the files against an uploaded index and writes
+ * out_path: a tab-separated header line, then one line per real top-k row
+ * "file scan spectrum rank pid nb ny hyperscore evalue n_scored" (file = index
+ * into paths, spectrum = index inside the file, hyperscore %.9g, evalue
+ * %.17g), rows of a spectrum consecutive and in rank order, spectra in no set
+ * order.  The rows are those hicops_search gives for the same spectra with
+ * tolerance prec_tol_da.  stats may be NULL.  Errors: HICOPS_EINVAL (NULL,
+ * bad config, unreadable file, malformed MS2 line (the message names file and
+ * line), unwritable output), search errors as hicops_search. */
+hicops_status hicops_pipeline_run(hicops_index* index, const char* const* paths, uint32_t n_paths,
+                                  const char* out_path, const hicops_pipeline_config* cfg,
+                                  hicops_pipeline_stats* stats);
+
+/* Parses one MS2 file (format above) into caller-owned host arrays:
+ * peak_off [n_spectra + 1], mz / intensity [n_peaks], prec_mz / charge /
+ * scan [n_spectra].  *n_spectra and *n_peaks are always set; the arrays are
+ * written only when they fit cap_spectra and cap_peaks (call once with caps
+ * 0 to size them).  Any array pointer may be NULL.  Errors: HICOPS_EINVAL
+ * (NULL, unreadable file, malformed line). */
+hicops_status hicops_ms2_read(const char* path, uint32_t cap_spectra, uint64_t cap_peaks, uint32_t* n_spectra,
+                              uint64_t* n_peaks, uint64_t* peak_off, float* mz, float* intensity,
+                              double* prec_mz, uint8_t* charge, uint32_t* scan);
+
+/* One step of double exponential smoothing (LaViola 2003, as the Task
+ * Scheduling section forecasts t_wait): s1 = a x + (1 - a) s1, s2 = a s1 +
+ * (1 - a) s2, both starting at the first sample (first != 0); returns the
+ * forecast of the next sample, (2 + a/(1-a)) s1 - (1 + a/(1-a)) s2.
+ * state [2] is the caller's. */
+double hicops_des_step(double* state, double x, double alpha, int first);
+
+/* The scheduling rules: an I worker turns to R when
+ * (t_wait >= t_min and t_cum + t_fct > t_max) or (the forward queue holds
+ * fewer than 5 buffers and no worker is in R); an R worker turns to I when
+ * (the queue holds 15 or more and more than one worker is in R) or the queue
+ * is full.  Return 1 for a move. */
+int hicops_sched_i_to_r(double t_wait, double t_cum, double t_fct, double t_min, double t_max, uint32_t qf_len,
+                        uint32_t n_r);
+int hicops_sched_r_to_i(uint32_t qf_len, uint32_t qf_cap, uint32_t n_r);
+
 /* Peptide pid: sequence (NUL-terminated, truncated to cap-1 letters), neutral
  * mass and the bitmask of positions carrying a variable modification (bit j =
  * residue j, 0-based).  Host only. */

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libhicops.so")
 
-CU_SOURCES = ["index_build.cu", "search.cu", "server.cu"]
+CU_SOURCES = ["index_build.cu", "search.cu", "server.cu", "pipeline.cu"]
 CPP_SOURCES = ["host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

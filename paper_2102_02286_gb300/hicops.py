@@ -93,6 +93,17 @@ assert PSM_DTYPE.itemsize == 32
 _lib = None
 
 
+class PipelineConfig(C.Structure):
+    _fields_ = [("batch_spectra", C.c_uint32), ("n_buffers", C.c_uint32), ("n_workers", C.c_uint32),
+                ("reserved", C.c_uint32), ("prec_tol_da", C.c_double), ("alpha", C.c_double),
+                ("t_min_s", C.c_double), ("t_max_s", C.c_double)]
+
+
+class PipelineStats(C.Structure):
+    _fields_ = [("spectra", C.c_uint64), ("batches", C.c_uint64), ("moves_i_to_r", C.c_uint64),
+                ("moves_r_to_i", C.c_uint64), ("seconds", C.c_double), ("wait_seconds", C.c_double)]
+
+
 def lib_path() -> str:
     return _build.LIB
 
@@ -140,6 +151,14 @@ def load(build_if_missing: bool = False):
         "hicops_index_copy_csr": (st, [P, P, P]),
         "hicops_index_free": (None, [P]),
         "hicops_last_error": (C.c_char_p, []),
+        "hicops_pipeline_run": (st, [P, P, C.c_uint32, C.c_char_p, C.POINTER(PipelineConfig),
+                                     C.POINTER(PipelineStats)]),
+        "hicops_ms2_read": (st, [C.c_char_p, C.c_uint32, C.c_uint64, C.POINTER(C.c_uint32),
+                                 C.POINTER(C.c_uint64), P, P, P, P, P, P]),
+        "hicops_des_step": (C.c_double, [P, C.c_double, C.c_double, C.c_int]),
+        "hicops_sched_i_to_r": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                          C.c_uint32, C.c_uint32]),
+        "hicops_sched_r_to_i": (C.c_int, [C.c_uint32, C.c_uint32, C.c_uint32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -496,3 +515,42 @@ def merge_shards_host(n_shards: int, n: int, top_k: int, psm: np.ndarray, hist: 
     _check(load().hicops_merge_shards(n_shards, n, top_k, _ptr(psm), _ptr(hist), _ptr(n_scored), hist_parts,
                                       evalue_mode, 0, None, _ptr(out.psm), _ptr(out.hist), _ptr(out.n_scored)))
     return out
+
+
+# ---- host ingest pipeline
+
+
+def run_files(index: "Index", paths, out_path: str, prec_tol_da: float, **cfg) -> PipelineStats:
+    """hicops_pipeline_run: searches every spectrum of the MS2 files and writes
+    the top-k rows to out_path (config fields as keyword arguments)."""
+    c = PipelineConfig(prec_tol_da=prec_tol_da, **cfg)
+    arr = (C.c_char_p * max(1, len(paths)))(*[os.fsencode(p) for p in paths])
+    stats = PipelineStats()
+    _check(load().hicops_pipeline_run(index.h, C.cast(arr, C.c_void_p), len(paths), os.fsencode(out_path),
+                                      C.byref(c), C.byref(stats)))
+    return stats
+
+
+def read_ms2(path: str) -> dict:
+    """hicops_ms2_read: the spectra of one MS2 file as arrays."""
+    L = load()
+    ns, npk = C.c_uint32(), C.c_uint64()
+    _check(L.hicops_ms2_read(os.fsencode(path), 0, 0, C.byref(ns), C.byref(npk), None, None, None, None, None,
+                             None))
+    n, m = ns.value, npk.value
+    out = {"peak_off": np.zeros(n + 1, np.uint64), "mz": np.zeros(m, np.float32),
+           "intensity": np.zeros(m, np.float32), "prec_mz": np.zeros(n, np.float64),
+           "charge": np.zeros(n, np.uint8), "scan": np.zeros(n, np.uint32)}
+    _check(L.hicops_ms2_read(os.fsencode(path), n, m, C.byref(ns), C.byref(npk), _ptr(out["peak_off"]),
+                             _ptr(out["mz"]), _ptr(out["intensity"]), _ptr(out["prec_mz"]), _ptr(out["charge"]),
+                             _ptr(out["scan"])))
+    return out
+
+
+def read_pipeline_rows(path: str) -> np.ndarray:
+    """The rows hicops_pipeline_run wrote, as a structured array."""
+    dt = np.dtype([("file", np.uint32), ("scan", np.uint32), ("spectrum", np.uint64), ("rank", np.uint32),
+                   ("pid", np.uint32), ("nb", np.uint32), ("ny", np.uint32), ("hyperscore", np.float32),
+                   ("evalue", np.float64), ("n_scored", np.uint32)])
+    rows = np.loadtxt(path, dtype=dt, delimiter="\t", skiprows=1, ndmin=1)
+    return rows

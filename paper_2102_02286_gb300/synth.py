@@ -218,6 +218,24 @@ def make_workload_inputs(w: Workload, n_spectra: Optional[int] = None):
     return prot, spec
 
 
+def write_ms2(spec: Spectra, path: str, sel=None, scan_base: int = 1) -> None:
+    """Writes spectra ``sel`` (all when None) as an MS2 text file: every
+    float32 peak and float64 precursor m/z written to round-trip exactly; a
+    spectrum of charge 0 gets no Z line."""
+    idx = range(spec.n) if sel is None else sel
+    with open(path, "w") as f:
+        f.write("H\tExtractor\tsynthetic\n")
+        for j, q in enumerate(idx):
+            a, e = int(spec.peak_off[q]), int(spec.peak_off[q + 1])
+            pm = float(spec.prec_mz[q])
+            z = int(spec.charge[q])
+            f.write(f"S\t{scan_base + j}\t{scan_base + j}\t{pm!r}\n")
+            if z:
+                f.write(f"Z\t{z}\t{(pm - 1.007276466812) * z + 1.007276466812:.6f}\n")
+            for m, i in zip(spec.mz[a:e], spec.intensity[a:e]):
+                f.write(str(np.float32(m)) + " " + str(np.float32(i)) + "\n")   # shortest float32 round-trip
+
+
 def spectra_from_lists(peaks, prec_mz, charge, tol) -> Spectra:
     """Hand-built batch (tests): ``peaks`` is a list of (mz list, intensity list)."""
     n = len(peaks)
