@@ -614,7 +614,7 @@ def run_ingest(args):
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "data": "synthetic",
         "config": {"workload": workload_desc(w), "spectra": n, "files": args.files, "file_bytes": file_bytes,
-                   "workers": workers, "batch_spectra": 4096, "buffers": 20},
+                   "workers": workers, "batch_spectra": 1024, "buffers": 20},
         "seconds_per_run": secs,
         "parse_only_spectra_per_s": n / parse_s,
         "in_memory_search_spectra_per_s": n / mem_s,

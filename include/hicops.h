@@ -300,7 +300,7 @@ hicops_status hicops_merge_shards(uint32_t n_shards, uint32_t n, uint32_t top_k,
  * hicops_sched_*), an I worker forecasting its next wait for the forward
  * queue by double exponential smoothing (hicops_des_step). */
 typedef struct hicops_pipeline_config {
-    uint32_t batch_spectra;   /* spectra per buffer (0 = 4096) */
+    uint32_t batch_spectra;   /* spectra per buffer (0 = 1024) */
     uint32_t n_buffers;       /* buffers in circulation (0 = 20; >= 2) */
     uint32_t n_workers;       /* R + I worker threads (0 = 4; >= 2); one starts as R */
     uint32_t reserved;        /* 0 */
@@ -319,8 +319,9 @@ typedef struct hicops_pipeline_stats {
 /* Searches every spectrum of the files against an uploaded index and writes
  * out_path: a tab-separated header line, then one line per real top-k row
  * "file scan spectrum rank pid nb ny hyperscore evalue n_scored" (file = index
- * into paths, spectrum = index inside the file, hyperscore %.9g, evalue
- * %.17g), rows of a spectrum consecutive and in rank order, spectra in no set
+ * into paths, spectrum = index inside the file; hyperscore and evalue in
+ * their shortest round-trip decimal form), rows of a spectrum consecutive and
+ * in rank order, spectra in no set
  * order.  The rows are those hicops_search gives for the same spectra with
  * tolerance prec_tol_da.  stats may be NULL.  Errors: HICOPS_EINVAL (NULL,
  * bad config, unreadable file, malformed MS2 line (the message names file and

@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cerrno>
+#include <charconv>
 #include <chrono>
 #include <condition_variable>
 #include <cstdio>
@@ -94,11 +95,12 @@ bool parse_ms2(const char* p, const char* e, uint64_t first_line, Ms2Parsed& out
                 // per-spectrum annotations: not used by the search
             } else {
                 if (!open) { err = "peak before any S line at line " + std::to_string(line); return false; }
-                char* end1 = nullptr;
-                const float m = strtof(q, &end1);
-                char* end2 = nullptr;
-                const float it = end1 ? strtof(end1, &end2) : 0.0f;
-                if (end1 == q || end2 == end1 || skip_ws(end2, le) != le) {
+                // two numbers, each correctly rounded to float32
+                float m = 0.0f, it = 0.0f;
+                const auto r1 = std::from_chars(q, le, m);
+                const char* q2 = r1.ec == std::errc() ? skip_ws(r1.ptr, le) : q;
+                const auto r2 = std::from_chars(q2, le, it);
+                if (r1.ec != std::errc() || q2 == r1.ptr || r2.ec != std::errc() || skip_ws(r2.ptr, le) != le) {
                     err = "malformed peak line at line " + std::to_string(line);
                     return false;
                 }
@@ -215,7 +217,7 @@ extern "C" hicops_status hicops_pipeline_run(hicops_index* idx, const char* cons
     if (!idx->dev.ready) { set_error("index has no device part (call hicops_index_upload)"); return HICOPS_EINVAL; }
     hicops_pipeline_config cfg{};
     if (cfg_in) cfg = *cfg_in;
-    if (!cfg.batch_spectra) cfg.batch_spectra = 4096;
+    if (!cfg.batch_spectra) cfg.batch_spectra = 1024;
     if (!cfg.n_buffers) cfg.n_buffers = 20;
     if (!cfg.n_workers) cfg.n_workers = 4;
     if (!(cfg.alpha > 0.0 && cfg.alpha < 1.0)) cfg.alpha = 0.5;
@@ -421,8 +423,16 @@ extern "C" hicops_status hicops_pipeline_run(hicops_index* idx, const char* cons
         q_f.cv.notify_all();
     };
 
-    // K: rows of every searched buffer, then the buffer back to q_r
+    // K: rows of every searched buffer, then the buffer back to q_r; numbers
+    // in their shortest round-trip decimal form
     std::thread writer([&] {
+        std::string text;
+        char num[64];
+        auto put_u = [&](uint64_t v, char sep) {
+            const auto r = std::to_chars(num, num + sizeof(num), v);
+            text.append(num, r.ptr);
+            text.push_back(sep);
+        };
         for (;;) {
             Buffer* b = nullptr;
             {
@@ -434,15 +444,29 @@ extern "C" hicops_status hicops_pipeline_run(hicops_index* idx, const char* cons
             }
             if (b->last) break;
             const uint32_t n = (uint32_t)b->sp.prec.size();
+            text.clear();
             for (uint32_t s = 0; s < n; ++s) {
                 for (uint32_t r = 0; r < k; ++r) {
                     const hicops_psm& o = b->psm[(size_t)s * k + r];
                     if (o.pid == 0xffffffffu) break;
-                    fprintf(out, "%u\t%u\t%llu\t%u\t%u\t%u\t%u\t%.9g\t%.17g\t%u\n", b->file, b->sp.scan[s],
-                            (unsigned long long)(b->first_spectrum + s), r, o.pid, o.nb, o.ny, o.hyperscore,
-                            o.evalue, b->ns[s]);
+                    put_u(b->file, '\t');
+                    put_u(b->sp.scan[s], '\t');
+                    put_u(b->first_spectrum + s, '\t');
+                    put_u(r, '\t');
+                    put_u(o.pid, '\t');
+                    put_u(o.nb, '\t');
+                    put_u(o.ny, '\t');
+                    auto rh = std::to_chars(num, num + sizeof(num), o.hyperscore);
+                    text.append(num, rh.ptr);
+                    text.push_back('\t');
+                    auto re = std::to_chars(num, num + sizeof(num), o.evalue);
+                    text.append(num, re.ptr);
+                    text.push_back('\t');
+                    put_u(b->ns[s], '\n');
                 }
             }
+            if (!text.empty() && fwrite(text.data(), 1, text.size(), out) != text.size())
+                fail(HICOPS_EINVAL, std::string("cannot write ") + out_path);
             q_r.push(b);
         }
     });
