@@ -153,3 +153,21 @@ def test_subset_indexes(lib):
     assert empty.stats().n_peptides == 0
     for h in (sub, empty):
         h.close()
+
+
+def test_lbe_parts_cover_the_database(lib):
+    from paper_2102_02286_gb300 import shard
+    w = configs.OPEN_MEDIUM.with_proteins(30)
+    prot = synth.make_proteome(w.n_proteins, w.db_seed, w.protein_len)
+    idx = hc.Index(prot.seq, prot.off, w.mods, w.params, upload=False)
+    P = idx.stats().n_peptides
+    parts = shard.lbe_parts(idx, 5, upload=False)
+    sizes = [p.stats().n_peptides for p in parts]
+    assert sum(sizes) == P and max(sizes) - min(sizes) <= 1
+    part = idx.partition_lbe(5)
+    for s, p in enumerate(parts):
+        mine = np.flatnonzero(part == s)
+        # every global pid of the part resolves on it, with the whole database's peptide
+        for g in mine[:: max(1, len(mine) // 10)]:
+            assert p.peptide(int(g)) == idx.peptide(int(g))
+        p.close()
