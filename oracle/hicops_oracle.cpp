@@ -70,9 +70,12 @@
 //      K*2^-31; fewer than 3 points or a <= 0 -> e = N.
 //
 // Parity pins: see tests/test_oracle_pins.py (closed forms, elemental
-// composition masses, brute force on tiny inputs, invariants).  Parity
-// unpinned: the absolute scale of the hyperscore, the histogram bin width and
-// the e-value fit window (R10-R12 are readings with no printed value).
+// composition masses, brute force on tiny inputs, invariants, library
+// routines, the Mod Distance worked example).  Parity unpinned: the absolute
+// scale of the hyperscore, the histogram bin width and the e-value fit
+// window (R10-R12), the smoothing window and order (R16), the log-Weibull
+// fitting method (R17) and the LBE cluster rule (R18) are readings with no
+// printed value.
 
 #include <cmath>
 #include <cstdint>
