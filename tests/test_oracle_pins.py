@@ -667,6 +667,22 @@ def test_evalue_variants_against_library_routines(oracle_lib, ev_mode):
         else:
             want = N * 10 ** (a * np.asarray(xs) + c)
         np.testing.assert_allclose(got, want, rtol=1e-8)
+    # mass in the first and last two bins: the histogram is 0 outside its bins
+    h = _binned_gumbel(20.0, 4.0, 10 ** 5)
+    h[0] += np.uint32(700)
+    h[1] += np.uint32(90)
+    h[254] += np.uint32(3)
+    h[255] += np.uint32(11)
+    keys = _keys([200.0, 60.0, 40.0])
+    got = oracle_lib.evalue(h, keys, np.arange(3, dtype=np.uint32), ev_mode)
+    g = h.astype(np.float64)
+    if ev_mode & 2:
+        g = np.rint(35 * signal.savgol_filter(g, 5, 2, mode="constant", cval=0.0))
+    x, y = _fit_points(g, ev_mode, min(255, int(keys[0]) >> 31))
+    a, c = np.polyfit(x, y, 1)
+    xs = np.array([200.0, 60.0, 40.0])
+    want = float(h.sum()) * (gumbel_r.sf(xs, loc=-c / a, scale=1 / a) if ev_mode & 1 else 10 ** (a * xs + c))
+    np.testing.assert_allclose(got, want, rtol=1e-8)
     # the smoothing changes the answer
     h = _binned_gumbel(30.0, 3.0, 10 ** 6)
     h[20] += np.uint32(40000)
