@@ -227,6 +227,21 @@ hicops_status hicops_search_work(hicops_index* index, const hicops_batch* batch,
 
 hicops_status hicops_index_get_stats(const hicops_index* index, hicops_index_stats* out);
 
+/* The parameters the index was built with. */
+hicops_status hicops_index_get_params(const hicops_index* index, hicops_params* out);
+
+/* Checkpoint of an index's host half (the digested database: peptide table,
+ * masses, modification tables, and a part's pid mapping) in one file at
+ * path, so a later process skips digestion (the paper writes its prepared
+ * data back for reuse, Superstep 2); hicops_index_load reads it back as a
+ * host-only index, and hicops_index_upload rebuilds the device half.  The
+ * format is fixed-width little-endian, versioned, and checked on load.
+ * Errors: HICOPS_EINVAL (NULL, unwritable / unreadable path, not a complete
+ * index file of this format, inconsistent contents, invalid parameters),
+ * HICOPS_ENOMEM. */
+hicops_status hicops_index_save(const hicops_index* index, const char* path);
+hicops_status hicops_index_load(const char* path, hicops_index** out);
+
 /* ---- database sharding (paper: every process searches its own partition of
  * the database, Superstep 3 and the Load Balancing section; the partial
  * score distributions are added and the results assembled, Superstep 4). */

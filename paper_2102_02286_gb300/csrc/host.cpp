@@ -8,8 +8,10 @@
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
+#include <cerrno>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <functional>
 #include <numeric>
 #include <thread>
@@ -352,6 +354,12 @@ extern "C" hicops_status hicops_build_index(const hicops_proteins* prot, const h
     return st;
 }
 
+extern "C" hicops_status hicops_index_get_params(const hicops_index* idx, hicops_params* out) {
+    if (!idx || !out) { set_error("NULL argument"); return HICOPS_EINVAL; }
+    *out = idx->p;
+    return HICOPS_OK;
+}
+
 extern "C" hicops_status hicops_index_get_stats(const hicops_index* idx, hicops_index_stats* out) {
     if (!idx || !out) { set_error("NULL argument"); return HICOPS_EINVAL; }
     *out = idx->stats;
@@ -511,4 +519,157 @@ extern "C" void hicops_index_free(hicops_index* idx) {
     if (!idx) return;
     hicops::free_device_index(idx);
     delete idx;
+}
+
+// ---- checkpoint: the host half of an index in one file (the paper writes
+// its preprocessed data back for reuse, Superstep 2); the device half is
+// rebuilt from it by hicops_index_upload.  Little-endian, fixed-width fields.
+
+namespace {
+
+constexpr char kIndexMagic[8] = {'H', 'I', 'C', 'O', 'P', 'S', 'I', 'X'};
+constexpr uint32_t kIndexFormat = 1;
+
+struct FileOut {
+    FILE* f;
+    bool ok = true;
+    void raw(const void* p, size_t n) {
+        if (ok && n && fwrite(p, 1, n, f) != n) ok = false;
+    }
+    template <class T>
+    void pod(const T& v) { raw(&v, sizeof(T)); }
+    template <class T>
+    void vec(const std::vector<T>& v) {
+        pod<uint64_t>(v.size());
+        raw(v.data(), v.size() * sizeof(T));
+    }
+};
+
+struct FileIn {
+    FILE* f;
+    uint64_t left;   // bytes not yet read
+    bool ok = true;
+    void raw(void* p, size_t n) {
+        if (!ok || n > left || (n && fread(p, 1, n, f) != n)) { ok = false; return; }
+        left -= n;
+    }
+    template <class T>
+    void pod(T& v) { raw(&v, sizeof(T)); }
+    template <class T>
+    void vec(std::vector<T>& v) {
+        uint64_t n = 0;
+        pod(n);
+        if (!ok || n > left / sizeof(T)) { ok = false; return; }   // never allocate past the file
+        v.resize(n);
+        raw(v.data(), n * sizeof(T));
+    }
+};
+
+}  // namespace
+
+extern "C" hicops_status hicops_index_save(const hicops_index* idx, const char* path) {
+    if (!idx || !path) { set_error("NULL argument"); return HICOPS_EINVAL; }
+    FILE* f = fopen(path, "wb");
+    if (!f) { set_error("cannot create %s: %s", path, strerror(errno)); return HICOPS_EINVAL; }
+    FileOut o{f};
+    o.raw(kIndexMagic, sizeof(kIndexMagic));
+    o.pod(kIndexFormat);
+    o.pod<uint32_t>(sizeof(hicops_params));
+    o.pod(idx->p);
+    o.raw(idx->mres, sizeof(idx->mres));
+    o.raw(idx->mmod, sizeof(idx->mmod));
+    o.raw(idx->var_type, sizeof(idx->var_type));
+    o.pod(idx->n_var);
+    o.vec(idx->var_delta);
+    o.vec(idx->var_max);
+    o.pod<uint64_t>(idx->residues.size());
+    o.raw(idx->residues.data(), idx->residues.size());
+    o.vec(idx->base_off);
+    o.vec(idx->mass);
+    o.vec(idx->base);
+    o.vec(idx->mask);
+    o.pod(idx->pid_stride);
+    o.pod(idx->pid_base);
+    o.vec(idx->pid_map);
+    o.pod(idx->n_bins);
+    o.pod(idx->s_max);
+    o.pod(idx->stats);
+    const bool closed = fclose(f) == 0;
+    if (!o.ok || !closed) { set_error("cannot write %s", path); return HICOPS_EINVAL; }
+    return HICOPS_OK;
+}
+
+extern "C" hicops_status hicops_index_load(const char* path, hicops_index** out) {
+    if (!path || !out) { set_error("NULL argument"); return HICOPS_EINVAL; }
+    *out = nullptr;
+    FILE* f = fopen(path, "rb");
+    if (!f) { set_error("cannot open %s: %s", path, strerror(errno)); return HICOPS_EINVAL; }
+    uint64_t size = 0;
+    if (fseek(f, 0, SEEK_END) == 0) {
+        const long e = ftell(f);
+        size = e > 0 ? (uint64_t)e : 0;
+    }
+    rewind(f);
+    std::unique_ptr<hicops_index> idx(new (std::nothrow) hicops_index());
+    if (!idx) { fclose(f); set_error("out of host memory"); return HICOPS_ENOMEM; }
+    FileIn in{f, size};
+    char magic[8] = {};
+    uint32_t format = 0, psize = 0;
+    in.raw(magic, sizeof(magic));
+    in.pod(format);
+    in.pod(psize);
+    const bool header = in.ok && memcmp(magic, kIndexMagic, sizeof(magic)) == 0 && format == kIndexFormat &&
+                        psize == sizeof(hicops_params);
+    if (header) {
+        in.pod(idx->p);
+        in.raw(idx->mres, sizeof(idx->mres));
+        in.raw(idx->mmod, sizeof(idx->mmod));
+        in.raw(idx->var_type, sizeof(idx->var_type));
+        in.pod(idx->n_var);
+        in.vec(idx->var_delta);
+        in.vec(idx->var_max);
+        uint64_t nres = 0;
+        in.pod(nres);
+        if (in.ok && nres <= in.left) {
+            idx->residues.resize(nres);
+            in.raw(&idx->residues[0], nres);
+        } else {
+            in.ok = false;
+        }
+        in.vec(idx->base_off);
+        in.vec(idx->mass);
+        in.vec(idx->base);
+        in.vec(idx->mask);
+        in.pod(idx->pid_stride);
+        in.pod(idx->pid_base);
+        in.vec(idx->pid_map);
+        in.pod(idx->n_bins);
+        in.pod(idx->s_max);
+        in.pod(idx->stats);
+    }
+    fclose(f);
+    if (!header || !in.ok || in.left != 0) {
+        set_error("%s is not a complete index file of this format", path);
+        return HICOPS_EINVAL;
+    }
+    // consistency of what was read: sizes, ranges and orders
+    hicops_index& x = *idx;
+    const size_t P = x.mass.size();
+    bool good = x.n_var == x.var_delta.size() && x.n_var == x.var_max.size() && !x.base_off.empty() &&
+                x.base_off.front() == 0 && x.base_off.back() == x.residues.size() && x.base.size() == P &&
+                x.mask.size() == P && x.pid_stride >= 1 && (x.pid_map.empty() || x.pid_map.size() == P) &&
+                P < (1ull << 31);
+    for (size_t i = 1; good && i < x.base_off.size(); ++i) good = x.base_off[i] >= x.base_off[i - 1];
+    for (size_t i = 0; good && i < 128; ++i) good = x.var_type[i] < (int)x.n_var;
+    for (size_t i = 0; good && i < P; ++i) {
+        good = x.base[i] + 1 < x.base_off.size() &&
+               x.base_off[x.base[i] + 1] - x.base_off[x.base[i]] <= kMaxLen && (i == 0 || x.mass[i] >= x.mass[i - 1]);
+    }
+    for (size_t i = 1; good && i < x.pid_map.size(); ++i) good = x.pid_map[i] > x.pid_map[i - 1];
+    if (!good) { set_error("%s: inconsistent index contents", path); return HICOPS_EINVAL; }
+    hicops_status st = validate_params(&x.p);
+    if (st != HICOPS_OK) return st;
+    x.dev = hicops::DeviceIndex{};
+    *out = idx.release();
+    return HICOPS_OK;
 }

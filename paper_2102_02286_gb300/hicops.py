@@ -8,6 +8,7 @@ PyTorch is used only for device memory and streams (``search_device``).
 from __future__ import annotations
 
 import ctypes as C
+import dataclasses
 import os
 from dataclasses import dataclass
 from typing import Optional, Sequence
@@ -15,6 +16,7 @@ from typing import Optional, Sequence
 import numpy as np
 
 from . import build as _build
+from .configs import SearchParams
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EOVERFLOW, EBUSY, ECANCELLED = range(8)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ETIMEOUT", "EOVERFLOW", "EBUSY", "ECANCELLED"]
@@ -145,6 +147,9 @@ def load(build_if_missing: bool = False):
         "hicops_index_shard": (st, [P, C.c_uint32, C.c_uint32, C.POINTER(P)]),
         "hicops_index_subset": (st, [P, P, C.c_uint64, C.POINTER(P)]),
         "hicops_partition_lbe": (st, [P, C.c_uint32, P]),
+        "hicops_index_get_params": (st, [P, C.POINTER(Params)]),
+        "hicops_index_save": (st, [P, C.c_char_p]),
+        "hicops_index_load": (st, [C.c_char_p, C.POINTER(P)]),
         "hicops_merge_shards": (st, [C.c_uint32, C.c_uint32, C.c_uint32, P, P, P, C.c_uint32, C.c_uint32, C.c_int,
                                      P, P, P, P]),
         "hicops_peptide": (st, [P, C.c_uint32, C.c_char_p, C.c_uint32, P, P]),
@@ -245,6 +250,25 @@ class Index:
         if upload:
             s.upload()
         return s
+
+    def save(self, path: str):
+        """hicops_index_save: the host half of the index to one file."""
+        _check(load().hicops_index_save(self.h, os.fsencode(path)))
+
+    @classmethod
+    def load(cls, path: str, upload: bool = True) -> "Index":
+        """hicops_index_load: an index saved by ``save`` (its device half rebuilt
+        when upload)."""
+        L = load()
+        h = C.c_void_p()
+        _check(L.hicops_index_load(os.fsencode(path), C.byref(h)))
+        p = Params()
+        _check(L.hicops_index_get_params(h, C.byref(p)))
+        sp = SearchParams(**{f.name: getattr(p, f.name) for f in dataclasses.fields(SearchParams)})
+        idx = cls._from_handle(h, sp)
+        if upload:
+            idx.upload()
+        return idx
 
     def partition_lbe(self, n_parts: int) -> np.ndarray:
         """hicops_partition_lbe: part[pid] of the load-balancing partition."""

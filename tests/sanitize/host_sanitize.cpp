@@ -4,7 +4,8 @@
 // (database, partition, search, e-values, edit and Mod Distance), built with
 // AddressSanitizer and UndefinedBehaviorSanitizer and driven through their
 // C entry points.  Results are checked too: the library's and the oracle's
-// LBE partitions agree, every part resolves its global pids.  The device
+// LBE partitions agree, every part resolves its global pids, a checkpoint
+// round-trips and every truncated checkpoint is rejected.  The device
 // half is replaced by stubs: nothing here touches a GPU.
 #include <cassert>
 #include <cmath>
@@ -156,6 +157,50 @@ int main(int argc, char** argv) {
     hicops_index* sh = nullptr;
     CHECK(hicops_index_shard(idx, 3, 1, &sh) == HICOPS_OK);
     hicops_index_free(sh);
+
+    // ---- checkpoint: round trip, then every truncation and a flipped byte of the file
+    const std::string ck = std::string(argv[2]) + "/db.hix";
+    CHECK(hicops_index_save(idx, ck.c_str()) == HICOPS_OK);
+    hicops_index* back = nullptr;
+    CHECK(hicops_index_load(ck.c_str(), &back) == HICOPS_OK);
+    {
+        char a[64], b[64];
+        double ma = 0, mb = 0;
+        uint64_t ka = 0, kb = 0;
+        CHECK(hicops_peptide(back, 7, a, sizeof(a), &ma, &ka) == HICOPS_OK);
+        CHECK(hicops_peptide(idx, 7, b, sizeof(b), &mb, &kb) == HICOPS_OK);
+        CHECK(strcmp(a, b) == 0 && ma == mb && ka == kb);
+    }
+    hicops_index_free(back);
+    std::string blob;
+    {
+        FILE* f = fopen(ck.c_str(), "rb");
+        CHECK(f != nullptr);
+        char buf[1 << 16];
+        size_t n;
+        while ((n = fread(buf, 1, sizeof(buf), f)) > 0) blob.append(buf, n);
+        fclose(f);
+    }
+    const std::string cut = std::string(argv[2]) + "/cut.hix";
+    for (size_t len = 0; len < blob.size(); len += 1 + len / 3) {
+        FILE* f = fopen(cut.c_str(), "wb");
+        CHECK(f != nullptr);
+        fwrite(blob.data(), 1, len, f);
+        fclose(f);
+        hicops_index* x = nullptr;
+        CHECK(hicops_index_load(cut.c_str(), &x) == HICOPS_EINVAL && x == nullptr);
+    }
+    for (size_t at : {size_t(20), size_t(200), blob.size() / 2, blob.size() - 5}) {
+        std::string bad = blob;
+        bad[at] = (char)(bad[at] ^ 0x5a);
+        FILE* f = fopen(cut.c_str(), "wb");
+        CHECK(f != nullptr);
+        fwrite(bad.data(), 1, bad.size(), f);
+        fclose(f);
+        hicops_index* x = nullptr;
+        const hicops_status s = hicops_index_load(cut.c_str(), &x);   // rejected, or a consistent index
+        if (s == HICOPS_OK) hicops_index_free(x);
+    }
 
     // ---- oracle: same database, same partition; a search; e-values
     OrMod omods[3] = {{"C", 57.021464, 0, 1}, {"M", 15.994915, 2, 0}, {"STY", 79.966331, 1, 0}};

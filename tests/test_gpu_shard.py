@@ -127,3 +127,13 @@ def test_lbe_parts_merge_to_the_unsharded_search_and_balance(setup, n_parts):
     assert cv < 0.05 and ccv > 4 * cv, (cv, ccv)
     for s in parts + chunks:
         s.close()
+
+
+def test_saved_index_searches_like_the_original(setup, tmp_path):
+    """A checkpointed index, loaded and uploaded again, gives the same results."""
+    torch, w, prot, idx, spec, ref = setup
+    path = str(tmp_path / "db.hix")
+    idx.save(path)
+    back = hc.Index.load(path)
+    _same(back.search(spec), ref)
+    back.close()

@@ -171,3 +171,50 @@ def test_lbe_parts_cover_the_database(lib):
         for g in mine[:: max(1, len(mine) // 10)]:
             assert p.peptide(int(g)) == idx.peptide(int(g))
         p.close()
+
+
+# ---------------------------------------------------------------- checkpoint (host only)
+
+
+def test_index_save_load_round_trip(lib, tmp_path):
+    w = configs.OPEN_MEDIUM.with_proteins(30)
+    prot = synth.make_proteome(w.n_proteins, w.db_seed, w.protein_len)
+    idx = hc.Index(prot.seq, prot.off, w.mods, w.params, upload=False)
+    path = str(tmp_path / "db.hix")
+    idx.save(path)
+    back = hc.Index.load(path, upload=False)
+    assert back.params == w.params
+    a, b = idx.stats(), back.stats()
+    assert (a.n_peptides, a.n_base_peptides, a.n_bins) == (b.n_peptides, b.n_base_peptides, b.n_bins)
+    for pid in range(0, a.n_peptides, max(1, a.n_peptides // 40)):
+        assert back.peptide(pid) == idx.peptide(pid)
+    np.testing.assert_array_equal(back.partition_lbe(3), idx.partition_lbe(3))
+    # a part keeps its global pids through a checkpoint
+    pids = np.flatnonzero(idx.partition_lbe(4) == 1).astype(np.uint32)
+    sub = idx.subset(pids, upload=False)
+    sub.save(path)
+    sub2 = hc.Index.load(path, upload=False)
+    assert sub2.peptide(int(pids[3])) == idx.peptide(int(pids[3]))
+    with pytest.raises(hc.HicopsError):
+        sub2.subset(pids[:2], upload=False)       # still a part
+    for h in (back, sub, sub2):
+        h.close()
+
+
+def test_index_load_rejects_bad_files(lib, tmp_path):
+    w = configs.TINY_CLOSED.with_proteins(20)
+    prot = synth.make_proteome(w.n_proteins, w.db_seed, w.protein_len)
+    idx = hc.Index(prot.seq, prot.off, w.mods, w.params, upload=False)
+    good = tmp_path / "db.hix"
+    idx.save(str(good))
+    data = good.read_bytes()
+    cases = {"missing": None, "empty": b"", "magic": b"X" + data[1:], "truncated": data[:-9],
+             "trailing": data + b"\0", "format": data[:8] + b"\x07" + data[9:]}
+    for name, blob in cases.items():
+        p = tmp_path / f"{name}.hix"
+        if blob is not None:
+            p.write_bytes(blob)
+        with pytest.raises(hc.HicopsError):
+            hc.Index.load(str(p), upload=False)
+    with pytest.raises(hc.HicopsError):
+        idx.save(str(tmp_path / "no_such_dir" / "x.hix"))
