@@ -160,7 +160,6 @@ struct Source {
     size_t pos = 0;                // next unread byte
     uint64_t line = 0, spectra = 0;
     bool loaded = false, done = false;
-    std::string err;
 };
 
 }  // namespace
