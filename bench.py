@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--workload", default="open_medium", choices=[w.name for w in configs.WORKLOADS])
+    ap.add_argument("--config", default="", help="a workload in JSON (configs.workload_to_json's form); "
+                                                 "replaces --workload")
     ap.add_argument("--spectra", type=int, default=0, help="override the workload's spectra per step")
     ap.add_argument("--proteins", type=int, default=0, help="override the workload's protein count")
     ap.add_argument("--oracle-spectra", type=int, default=3, help="CPU-baseline sample size")
@@ -69,7 +71,11 @@ def parse():
 
 
 def workload(args):
-    w = configs.BY_NAME[args.workload]
+    if args.config:
+        with open(args.config) as f:
+            w = configs.workload_from_json(f.read())
+    else:
+        w = configs.BY_NAME[args.workload]
     if args.proteins:
         w = w.with_proteins(args.proteins)
     if args.spectra:

@@ -1,4 +1,4 @@
-"""The five synthetic search workloads, as plain data.
+"""The synthetic search workloads, as plain data (and as JSON).
 
 Each workload names the proteome recipe, the digestion and modification
 rules, the query-spectrum recipe and the search parameters.  The numbers
@@ -9,7 +9,8 @@ computes anything; both the CUDA path and the CPU oracle read these values.
 """
 from __future__ import annotations
 
-from dataclasses import dataclass, field, replace
+import json
+from dataclasses import asdict, dataclass, field, replace
 from typing import List, Optional, Tuple
 
 # Base seed: the paper's arXiv number; workload i uses BASE_SEED + i.
@@ -158,3 +159,39 @@ OPEN_MEDIUM_TOL = Workload(
 
 WORKLOADS: List[Workload] = [TINY_CLOSED, OPEN_MEDIUM, OPEN_LARGE, UNEVEN_BATCHED, SERVING_STREAM, OPEN_MEDIUM_TOL]
 BY_NAME = {w.name: w for w in WORKLOADS}
+
+
+
+# ---- JSON form of a workload (a user's own workload for bench.py --config)
+
+
+def workload_to_json(w: Workload) -> str:
+    """The workload as a JSON object: every field of the workload, its
+    modification rules, search parameters and spectrum recipe."""
+    return json.dumps(asdict(w), indent=1)
+
+
+def workload_from_json(text: str) -> Workload:
+    """A workload from ``workload_to_json``'s form; fields left out take their
+    defaults, unknown fields are an error."""
+    d = json.loads(text)
+    if not isinstance(d, dict):
+        raise ValueError("a workload is a JSON object")
+    d = dict(d)
+    mods = tuple(Mod(**m) for m in d.pop("mods", []))
+    params = SearchParams(**d.pop("params", {}))
+    rec = dict(d.pop("spectra", {}))
+    for k in ("target_peaks", "charges", "tol_da"):
+        if rec.get(k) is not None:
+            rec[k] = tuple(rec[k])
+    spectra = SpectraRecipe(**rec)
+    if "protein_len" in d:
+        d["protein_len"] = tuple(d["protein_len"])
+    return Workload(mods=mods, params=params, spectra=spectra, **d)
+
+
+if __name__ == "__main__":
+    import sys
+    if len(sys.argv) != 2 or sys.argv[1] not in BY_NAME:
+        raise SystemExit("usage: python -m paper_2102_02286_gb300.configs <workload name>  (prints its JSON)")
+    print(workload_to_json(BY_NAME[sys.argv[1]]))

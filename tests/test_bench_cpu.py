@@ -33,3 +33,14 @@ def test_reference_arm_line():
 
 def test_reference_arm_other_ranks_are_silent():
     assert run_bench({"RANK": "1", "WORLD_SIZE": "2"}, "--workload", "tiny_closed", "--steps", "1") == []
+
+
+def test_reference_arm_with_a_json_workload(tmp_path):
+    from paper_2102_02286_gb300 import configs
+    w = configs.TINY_CLOSED.with_proteins(60)
+    w = configs.workload_from_json(configs.workload_to_json(w).replace('"tiny_closed"', '"my_workload"'))
+    cfg = tmp_path / "w.json"
+    cfg.write_text(configs.workload_to_json(w))
+    lines = run_bench({}, "--config", str(cfg), "--steps", "1", "--warmup", "0", "--oracle-spectra", "3")
+    d = json.loads(lines[0])
+    assert d["config"]["workload"].startswith("my_workload")
