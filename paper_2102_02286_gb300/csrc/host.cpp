@@ -666,9 +666,24 @@ extern "C" hicops_status hicops_index_load(const char* path, hicops_index** out)
                x.base_off[x.base[i] + 1] - x.base_off[x.base[i]] <= kMaxLen && (i == 0 || x.mass[i] >= x.mass[i - 1]);
     }
     for (size_t i = 1; good && i < x.pid_map.size(); ++i) good = x.pid_map[i] > x.pid_map[i - 1];
+    // every residue byte indexes the 128-entry mass tables on the device and
+    // must be a letter with a mass (digestion keeps no other)
+    for (size_t i = 0; good && i < x.residues.size(); ++i) {
+        const unsigned char c = (unsigned char)x.residues[i];
+        good = c < 128 && x.mres[c] > 0.0 && std::isfinite(x.mres[c]) && std::isfinite(x.mmod[c]);
+    }
     if (!good) { set_error("%s: inconsistent index contents", path); return HICOPS_EINVAL; }
     hicops_status st = validate_params(&x.p);
     if (st != HICOPS_OK) return st;
+    // the bin count and the largest S follow from the parameters, as in
+    // hicops_digest; a file that disagrees would size the device tables wrongly
+    const uint32_t n_bins = (uint32_t)std::floor(x.p.frag_mz_max / x.p.bin_width_da) + 1;
+    const uint64_t s_max = std::min<uint64_t>(query_bins_cap(x.p), 2ull * (x.p.max_len - 1)) * x.p.intensity_scale;
+    if (x.n_bins != n_bins || x.s_max != s_max) {
+        set_error("%s: stored bin count %u / largest S %llu disagree with the parameters (%u / %llu)", path,
+                  x.n_bins, (unsigned long long)x.s_max, n_bins, (unsigned long long)s_max);
+        return HICOPS_EINVAL;
+    }
     x.dev = hicops::DeviceIndex{};
     *out = idx.release();
     return HICOPS_OK;

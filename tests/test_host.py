@@ -218,3 +218,40 @@ def test_index_load_rejects_bad_files(lib, tmp_path):
             hc.Index.load(str(p), upload=False)
     with pytest.raises(hc.HicopsError):
         idx.save(str(tmp_path / "no_such_dir" / "x.hix"))
+
+
+def test_index_load_rejects_tampered_fields(lib, tmp_path):
+    # fields the device half trusts: the bin count and largest S (they size
+    # the bucket tables and the LS table) and the residue bytes (they index
+    # the 128-entry mass tables of the ion generator)
+    import struct
+    w = configs.TINY_CLOSED.with_proteins(20)
+    prot = synth.make_proteome(w.n_proteins, w.db_seed, w.protein_len)
+    idx = hc.Index(prot.seq, prot.off, w.mods, w.params, upload=False)
+    good = tmp_path / "db.hix"
+    idx.save(str(good))
+    data = bytearray(good.read_bytes())
+    hc.Index.load(str(good), upload=False).close()
+    tail = C.sizeof(hc.IndexStats)
+    at_sm, at_nb = len(data) - tail - 8, len(data) - tail - 12
+    n_bins = struct.unpack_from("<I", data, at_nb)[0]
+    s_max = struct.unpack_from("<Q", data, at_sm)[0]
+    assert n_bins == idx.stats().n_bins
+    # n_var = 0 for this workload: two empty vectors before the residue count
+    at_res = 16 + C.sizeof(hc.Params) + 1024 + 1024 + 128 + 4 + 8 + 8 + 8
+    assert chr(data[at_res]) in "ACDEFGHIKLMNPQRSTVWY"
+    cases = {"n_bins_small": (at_nb, struct.pack("<I", n_bins // 2)),
+             "n_bins_large": (at_nb, struct.pack("<I", n_bins + 1)),
+             "s_max_small": (at_sm, struct.pack("<Q", s_max - 1)),
+             "s_max_huge": (at_sm, struct.pack("<Q", 1 << 60)),
+             "residue_high": (at_res, bytes([0xC1])),
+             "residue_no_mass": (at_res, b"B")}
+    for name, (at, blob) in cases.items():
+        bad = bytearray(data)
+        bad[at:at + len(blob)] = blob
+        p = tmp_path / f"{name}.hix"
+        p.write_bytes(bytes(bad))
+        with pytest.raises(hc.HicopsError) as e:
+            hc.Index.load(str(p), upload=False)
+        assert e.value.status == hc.EINVAL, name
+    idx.close()
