@@ -98,7 +98,9 @@ typedef struct hicops_params {
      * (Superstep 4, Supplementary Algorithm 4): 0 = the linear tail fit;
      * HICOPS_EVALUE_LOG_WEIBULL = the log-Weibull (Gumbel) fit instead;
      * HICOPS_EVALUE_SMOOTH = either fit on the histogram smoothed by the
-     * 5-point quadratic Savitzky-Golay filter.  Other bits: HICOPS_EINVAL. */
+     * 5-point quadratic Savitzky-Golay filter.  Other bits: HICOPS_EINVAL.
+     * Superstep 4's own order, smoothing then the tail fit, is
+     * HICOPS_EVALUE_SMOOTH (the Python workloads' default). */
     uint32_t evalue_mode;
     uint32_t reserved;   /* 0 */
 } hicops_params;
@@ -212,7 +214,9 @@ hicops_status hicops_search(hicops_index* index, const hicops_batch* batch, hico
  * wrong results: order them, e.g. on one stream.  The first call on each
  * device looks up the array's device address (which may load the library's
  * device code on that device); make that first call before any stream
- * capture begins.
+ * capture begins.  The looked-up address belongs to the device's context:
+ * after that context is replaced (cudaDeviceReset), the next call looks it up
+ * again, so make that call before any stream capture too.
  * Errors: HICOPS_EINVAL (more than HICOPS_NOALLOC_MAX_SPECTRA spectra, host
  * pointers, the hicops_search cases), HICOPS_ECUDA. */
 hicops_status hicops_search_noalloc(hicops_index* index, const hicops_batch* batch, hicops_psm* out_psm,

@@ -57,8 +57,10 @@ class SearchParams:
     hist_bins: int = 256
     intensity_scale: int = 10000
     # e-value: bit 0 = log-Weibull (Gumbel) fit instead of the linear tail
-    # fit, bit 1 = Savitzky-Golay smoothing of the histogram before the fit
-    evalue_mode: int = 0
+    # fit, bit 1 = Savitzky-Golay smoothing of the histogram before the fit.
+    # Default 2: Superstep 4 smooths the assembled distribution first, then
+    # fits its tail
+    evalue_mode: int = 2
     max_total_mods: int = 0        # 0 = no global cap
 
 

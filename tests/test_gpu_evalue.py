@@ -38,7 +38,7 @@ def build_both(oracle_lib, w):
     return prot, idx, db
 
 
-@pytest.mark.parametrize("ev_mode", [1, 2, 3])
+@pytest.mark.parametrize("ev_mode", [0, 1, 2, 3])
 def test_evalue_options_closed(gpu, oracle_lib, ev_mode):
     w = with_mode(configs.TINY_CLOSED, ev_mode).with_proteins(200).with_spectra(300)
     prot, idx, db = build_both(oracle_lib, w)
