@@ -586,20 +586,51 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 std::mutex g_noalloc_mu;
 void* g_noalloc_base[kNoAllocDevices] = {};
+unsigned long long g_noalloc_ctx[kNoAllocDevices] = {};   // context the address belongs to
+
+// Unique id of the calling thread's current context (the driver's
+// cuCtxGetId, reached through the runtime), or 0 when there is none or the
+// driver cannot tell.  Ids are never reused within a process, unlike
+// context handles.
+unsigned long long current_context_id() {
+    using GetCurrent = int (*)(void**);
+    using GetId = int (*)(void*, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+    });
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&ctx) == 0 && ctx && get_id(ctx, &id) == 0) return id;
+    return 0;
+}
 
 // Device address of the array on device dev, which must be current.  The
 // first call on a device looks it up (this can load the module on that
-// device).
+// device), and so does the first call after the device's context was
+// replaced (cudaDeviceReset), because the address belongs to the context.
 hicops_status noalloc_scratch(int dev, unsigned char** out) {
     if (dev < 0 || dev >= kNoAllocDevices) {
         set_error("hicops_search_noalloc serves device ordinals below %d, not %d", kNoAllocDevices, dev);
         return HICOPS_EINVAL;
     }
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_base[dev]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_noalloc_base[dev] || ctx == 0 || ctx != g_noalloc_ctx[dev]) {
         void* p = nullptr;
         HC_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
         g_noalloc_base[dev] = p;
+        g_noalloc_ctx[dev] = current_context_id();   // the lookup may have created the context
     }
     *out = static_cast<unsigned char*>(g_noalloc_base[dev]);
     return HICOPS_OK;

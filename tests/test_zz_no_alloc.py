@@ -1,5 +1,7 @@
 """hicops_search_noalloc: the search with its scratch in a fixed device array
 gives exactly what hicops_search gives, call after call, without allocating."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -86,3 +88,44 @@ def test_rejects_batches_over_the_limit(setup):
     # an empty batch is a no-op
     empty = spec.subset([])
     idx.search_noalloc(hc.DeviceBatch.from_spectra(empty), hc.DeviceResult.alloc(1, w.params.top_k))
+
+
+def _limit_case(case):
+    """A 64-spectrum batch (the limit) of a configuration that stresses the
+    scratch: many work units per spectrum (seg_pids set, so hicops_search
+    splits windows into up to 64 units where the fixed array allows 16), or
+    the widest query-bin stride (fragment tolerance of 1 bin on 341 retained
+    peaks: 1,023 bins a spectrum)."""
+    if case == "seg_pids":
+        w = configs.UNEVEN_BATCHED.with_proteins(400).with_spectra(NOALLOC_MAX)
+        cfg = hc.SearchConfig(0, 0, 0, 1 << 10)
+    else:
+        w = configs.OPEN_MEDIUM_TOL.with_proteins(300).with_spectra(NOALLOC_MAX)
+        w = dataclasses.replace(w, params=dataclasses.replace(w.params, top_n_peaks=341),
+                                spectra=dataclasses.replace(w.spectra, target_peaks=(380, 500)))
+        cfg = None
+    return w, cfg
+
+
+@pytest.mark.parametrize("case", ["seg_pids", "tol_widest"])
+def test_matches_hicops_search_at_the_limit(setup, case):
+    torch = setup[0]
+    w, cfg = _limit_case(case)
+    prot = synth.make_proteome(w.n_proteins, w.db_seed)
+    idx = hc.Index(prot.seq, prot.off, w.mods, w.params)
+    if cfg is not None:
+        idx.set_config(cfg)
+    spec = synth.make_spectra(prot, w)
+    assert spec.n == NOALLOC_MAX
+    exp = idx.search(spec)
+    assert int(exp.n_scored.sum()) > 0
+    db = hc.DeviceBatch.from_spectra(spec)
+    out = hc.DeviceResult.alloc(spec.n, w.params.top_k)
+    for _ in range(2):                      # two calls in a row on the shared array
+        out.psm.zero_()
+        out.hist.zero_()
+        out.n_scored.zero_()
+        idx.search_noalloc(db, out)
+        torch.cuda.synchronize()
+        _same(out.to_host(spec.n, w.params.top_k), exp)
+    idx.close()
