@@ -514,8 +514,12 @@ class Server:
             pass
 
 
+# the e-value mode of the workloads' search parameters (smoothing, then the tail fit)
+EVALUE_DEFAULT = 2
+
+
 def merge_shards(n_shards: int, n: int, top_k: int, psm, hist, n_scored, hist_parts: int,
-                 stream=None, evalue_mode: int = 0) -> "DeviceResult":
+                 stream=None, evalue_mode: int = EVALUE_DEFAULT) -> "DeviceResult":
     """hicops_merge_shards on device tensors (asynchronous on the stream):
     psm [n_shards * n * top_k] rows, hist [hist_parts * n * 256], n_scored
     [hist_parts * n]; returns a DeviceResult of the merged search."""
@@ -529,7 +533,7 @@ def merge_shards(n_shards: int, n: int, top_k: int, psm, hist, n_scored, hist_pa
 
 
 def merge_shards_host(n_shards: int, n: int, top_k: int, psm: np.ndarray, hist: np.ndarray,
-                      n_scored: np.ndarray, hist_parts: int, evalue_mode: int = 0) -> SearchResult:
+                      n_scored: np.ndarray, hist_parts: int, evalue_mode: int = EVALUE_DEFAULT) -> SearchResult:
     """hicops_merge_shards on host arrays (the library copies to the device and back)."""
     psm = np.ascontiguousarray(psm, PSM_DTYPE)
     hist = np.ascontiguousarray(hist, np.uint32)

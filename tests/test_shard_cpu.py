@@ -38,7 +38,7 @@ def reference_merge(oracle, parts, hist_sum, k):
         out[q]["key"] = np.iinfo(np.int64).min
         out[q]["evalue"] = np.inf
         out[q][:len(top)] = top
-        ev = oracle.evalue(hist_sum[q], out[q]["key"], out[q]["pid"])
+        ev = oracle.evalue(hist_sum[q], out[q]["key"], out[q]["pid"], W.params.evalue_mode)
         out[q]["evalue"] = ev
     return out
 
