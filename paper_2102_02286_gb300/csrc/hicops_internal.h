@@ -44,8 +44,10 @@ struct DeviceIndex {
     bool ready = false;
     int device = -1;
     double* mass = nullptr;        // [P] neutral mass, pid order
-    uint64_t* off = nullptr;       // [n_bins + 1] bucket offsets
-    uint32_t* entry = nullptr;     // [E] pid << 1 | isY, pid ascending in a bucket
+    uint64_t* off = nullptr;       // [n_bins + 1] bucket offsets (multiples of 4)
+    uint32_t* entry = nullptr;     // [n_stored + 4] pid << 1 | isY, pid ascending in a bucket; each
+                                   // bucket padded to a multiple of 4 with 0xffffffff (16-byte groups)
+    uint64_t n_stored = 0;         // entries including the pads (off[n_bins])
     int64_t* lf = nullptr;         // [kMaxLen + 1] LF[n] = round(2^32 log10 n!)
     int64_t* ls = nullptr;         // [s_max + 1]   LS[s] = round(2^32 log10 s)
     // chunk skip table of every non-empty bucket: row[bin] (-1 empty) and

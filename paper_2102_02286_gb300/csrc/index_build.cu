@@ -6,6 +6,7 @@
 // stable LSD radix sort by bin over (bin, pid, isY) keys emitted in pid
 // order, so each bucket comes out pid-ascending without a comparison sort.
 #include <algorithm>
+#include <new>
 #include <cmath>
 #include <chrono>
 #include <vector>
@@ -202,9 +203,22 @@ __global__ void bucket_off_kernel(const uint64_t* __restrict__ keys, uint64_t n,
     for (int64_t b = prev + 1; b <= cur; ++b) off[b] = i;
 }
 
-__global__ void take_low_kernel(const uint64_t* __restrict__ keys, uint64_t n, uint32_t* __restrict__ entry) {
+// Bucket sizes rounded up to whole groups of 4 entries (16 bytes), so that
+// every bucket starts 16-byte aligned in the entry array.
+__global__ void padded_size_kernel(const uint64_t* __restrict__ off, uint32_t nbins, uint32_t* __restrict__ psz) {
+    const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nbins) psz[b] = (uint32_t)((off[b + 1] - off[b] + 3) & ~3ull);
+}
+
+// entry[poff[bin] + rank in bucket] = pid << 1 | isY; the up to 3 slots after
+// a bucket's last entry keep the pad value 0xffffffff (pid 2^31 - 1, above
+// every peptide id, so a bucket stays pid-sorted and no window contains it).
+__global__ void take_low_kernel(const uint64_t* __restrict__ keys, uint64_t n, const uint64_t* __restrict__ off,
+                                const uint64_t* __restrict__ poff, uint32_t* __restrict__ entry) {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) entry[i] = (uint32_t)keys[i];
+    if (i >= n) return;
+    const uint32_t bin = (uint32_t)(keys[i] >> 32);
+    entry[poff[bin] + (i - off[bin])] = (uint32_t)keys[i];
 }
 
 __global__ void bucket_max_kernel(const uint64_t* __restrict__ off, uint32_t nbins, unsigned long long* mx) {
@@ -393,34 +407,48 @@ hicops_status upload_index(hicops_index* idx) {
             std::swap(keys, keys2);
         }
     }
-    // one spare word: the allocation is never empty
-    HC_CUDA(cudaMalloc(&d.entry, sizeof(uint32_t) * (E + 1)));
-    if (E) take_low_kernel<<<(unsigned)((E + 255) / 256), 256, 0, s>>>(keys, E, d.entry);
-    bucket_off_kernel<<<(unsigned)((E + 1 + 255) / 256), 256, 0, s>>>(keys, E, idx->n_bins, d.off);
+    // bucket offsets of the sorted keys (uoff), then the stored layout: each
+    // bucket padded to a multiple of 4 entries (d.off), so that the search
+    // reads whole 16-byte groups
+    const uint32_t nb = idx->n_bins;
+    const unsigned bgrid = (nb + 255) / 256;
+    const unsigned egrid = (unsigned)((E + 255) / 256);
+    uint64_t* uoff;
+    HC_CUDA(dalloc(&uoff, (uint64_t)nb + 1, tf.ptrs));
+    bucket_off_kernel<<<(unsigned)((E + 1 + 255) / 256), 256, 0, s>>>(keys, E, nb, uoff);
     HC_CUDA(cudaGetLastError());
     unsigned long long* d_mx = (unsigned long long*)d_total;
     HC_CUDA(cudaMemsetAsync(d_mx, 0, sizeof(uint64_t), s));
-    bucket_max_kernel<<<(idx->n_bins + 255) / 256, 256, 0, s>>>(d.off, idx->n_bins, d_mx);
+    bucket_max_kernel<<<bgrid, 256, 0, s>>>(uoff, nb, d_mx);
     HC_CUDA(cudaGetLastError());
     uint64_t mx = 0;
     HC_CUDA(cudaMemcpyAsync(&mx, d_mx, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
     HC_CUDA(cudaStreamSynchronize(s));
-    if (mx >= (1ull << 32)) {
-        set_error("a bucket holds %llu entries (limit 2^32)", (unsigned long long)mx);
+    if (mx >= (1ull << 32) - 3) {
+        set_error("a bucket holds %llu entries (limit 2^32 - 4)", (unsigned long long)mx);
         return HICOPS_EOVERFLOW;
     }
-
-    // chunk skip tables for every non-empty bucket
-    const uint32_t nb = idx->n_bins;
-    const unsigned bgrid = (nb + 255) / 256;
-    const unsigned egrid = (unsigned)((E + 255) / 256);
     uint32_t* flag;
     uint64_t *rscan, *rtotal, *btmp;
     HC_CUDA(dalloc(&flag, nb, tf.ptrs));
     HC_CUDA(dalloc(&rscan, nb, tf.ptrs));
     HC_CUDA(dalloc(&rtotal, 1, tf.ptrs));
     HC_CUDA(dalloc(&btmp, scan_tmp_words(nb), tf.ptrs));
-    bucket_flag_kernel<<<bgrid, 256, 0, s>>>(d.off, nb, 1, flag);
+    padded_size_kernel<<<bgrid, 256, 0, s>>>(uoff, nb, flag);
+    HC_CUDA(cudaGetLastError());
+    HC_CUDA(exclusive_scan<uint32_t>(flag, nb, d.off, d.off + nb, btmp, s));
+    uint64_t Ep = 0;
+    HC_CUDA(cudaMemcpyAsync(&Ep, d.off + nb, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    HC_CUDA(cudaStreamSynchronize(s));
+    // four spare words: the allocation is never empty and ends 16-byte aligned
+    HC_CUDA(cudaMalloc(&d.entry, sizeof(uint32_t) * (Ep + 4)));
+    HC_CUDA(cudaMemsetAsync(d.entry, 0xff, sizeof(uint32_t) * (Ep + 4), s));
+    if (E) take_low_kernel<<<egrid, 256, 0, s>>>(keys, E, uoff, d.off, d.entry);
+    HC_CUDA(cudaGetLastError());
+
+    // chunk skip tables for every non-empty bucket (positions relative to
+    // the bucket start, so the same in both layouts)
+    bucket_flag_kernel<<<bgrid, 256, 0, s>>>(uoff, nb, 1, flag);
     HC_CUDA(cudaGetLastError());
     HC_CUDA(exclusive_scan<uint32_t>(flag, nb, rscan, rtotal, btmp, s));
     HC_CUDA(cudaMalloc(&d.skip_row, sizeof(int32_t) * nb));
@@ -431,12 +459,12 @@ hicops_status upload_index(hicops_index* idx) {
     HC_CUDA(cudaStreamSynchronize(s));
     d.skip_stride = (uint32_t)(((P + kChunk - 1) >> kChunkShift) + 1);
     HC_CUDA(cudaMalloc(&d.skip, sizeof(uint32_t) * (rows ? rows : 1) * d.skip_stride));
-    if (E) skip_fill_kernel<<<egrid, 256, 0, s>>>(keys, E, d.off, d.skip_row, d.skip_stride, d.skip);
+    if (E) skip_fill_kernel<<<egrid, 256, 0, s>>>(keys, E, uoff, d.skip_row, d.skip_stride, d.skip);
     HC_CUDA(cudaGetLastError());
 
     // hot buckets as bitmaps
     const uint64_t hot_lo = std::max<uint64_t>(2, P >> kHotShift);
-    bucket_flag_kernel<<<bgrid, 256, 0, s>>>(d.off, nb, hot_lo, flag);
+    bucket_flag_kernel<<<bgrid, 256, 0, s>>>(uoff, nb, hot_lo, flag);
     HC_CUDA(cudaGetLastError());
     HC_CUDA(exclusive_scan<uint32_t>(flag, nb, rscan, rtotal, btmp, s));
     HC_CUDA(cudaMalloc(&d.hot_id, sizeof(int32_t) * nb));
@@ -460,7 +488,8 @@ hicops_status upload_index(hicops_index* idx) {
     HC_CUDA(cudaGetLastError());
     HC_CUDA(cudaStreamSynchronize(s));
 
-    d.bytes = sizeof(double) * P + sizeof(uint64_t) * (idx->n_bins + 1) + sizeof(uint32_t) * E +
+    d.n_stored = Ep;
+    d.bytes = sizeof(double) * P + sizeof(uint64_t) * (idx->n_bins + 1) + sizeof(uint32_t) * (Ep + 4) +
               sizeof(int64_t) * (lf.size() + ls.size()) + sizeof(int32_t) * 2 * nb +
               sizeof(uint32_t) * rows * d.skip_stride + 2 * hbytes;
     idx->stats.n_entries = E;
@@ -480,10 +509,31 @@ extern "C" hicops_status hicops_index_upload(hicops_index* idx) {
     return st;
 }
 
+// The device keeps every bucket padded to a multiple of 4 entries; the copy
+// leaves the pad slots out, so buckets are back to back as documented.
 extern "C" hicops_status hicops_index_copy_csr(const hicops_index* idx, uint64_t* off, uint32_t* entries) {
     if (!idx || !idx->dev.ready) { hicops::set_error("index not uploaded"); return HICOPS_EINVAL; }
-    if (off) HC_CUDA(cudaMemcpy(off, idx->dev.off, sizeof(uint64_t) * (idx->n_bins + 1), cudaMemcpyDeviceToHost));
-    if (entries && idx->stats.n_entries)
-        HC_CUDA(cudaMemcpy(entries, idx->dev.entry, sizeof(uint32_t) * idx->stats.n_entries, cudaMemcpyDeviceToHost));
+    if (!off && !entries) return HICOPS_OK;
+    const uint32_t nb = idx->n_bins;
+    std::vector<uint64_t> poff(nb + 1);
+    std::vector<uint32_t> pent;
+    try {
+        pent.resize(idx->dev.n_stored);
+    } catch (const std::bad_alloc&) {
+        hicops::set_error("out of host memory");
+        return HICOPS_ENOMEM;
+    }
+    HC_CUDA(cudaMemcpy(poff.data(), idx->dev.off, sizeof(uint64_t) * (nb + 1), cudaMemcpyDeviceToHost));
+    if (!pent.empty())
+        HC_CUDA(cudaMemcpy(pent.data(), idx->dev.entry, sizeof(uint32_t) * pent.size(), cudaMemcpyDeviceToHost));
+    uint64_t o = 0;
+    for (uint32_t b = 0; b < nb; ++b) {
+        if (off) off[b] = o;
+        for (uint64_t i = poff[b]; i < poff[b + 1] && pent[i] != 0xffffffffu; ++i) {
+            if (entries) entries[o] = pent[i];
+            ++o;
+        }
+    }
+    if (off) off[nb] = o;
     return HICOPS_OK;
 }

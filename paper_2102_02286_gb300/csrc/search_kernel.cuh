@@ -154,8 +154,19 @@ __device__ __forceinline__ uint32_t counter_inc_y(uint32_t isy, uint32_t iq) {
 
 __device__ __forceinline__ uint32_t slot_of(uint32_t off) { return (off * 2654435761u) >> 22; }   // 10 bits
 
-// Exclusive scan of the ordinary peaks' run lengths, in two halves around a
-// barrier the caller provides.  Thread tid owns peaks tid*ppt .. +ppt-1.
+// A run [ra, rb) of a bucket (positions relative to its 16-byte aligned
+// start) is read as whole groups of 4 entries: from ra rounded down to a
+// multiple of 4 to rb rounded up.  The extra entries at either end lie in the
+// same bucket outside the run's columns, or are the bucket's pad slots; both
+// fall outside every peptide range the run is searched for.
+__device__ __forceinline__ uint32_t group_start(uint32_t ra) { return ra & ~3u; }
+__device__ __forceinline__ uint32_t group_len(uint32_t ra, uint32_t rb) {
+    return ra == rb ? 0u : ((rb + 3u) & ~3u) - (ra & ~3u);
+}
+
+// Exclusive scan of the ordinary peaks' run lengths (in whole groups), in two
+// halves around a barrier the caller provides.  Thread tid owns peaks
+// tid*ppt .. +ppt-1.
 template <int PPT>
 __device__ __forceinline__ uint32_t scan_runs_1(SearchShared& sh, int nnorm, int ppt, const uint32_t (&ra)[PPT],
                                                 const uint32_t (&rb)[PPT]) {
@@ -164,7 +175,7 @@ __device__ __forceinline__ uint32_t scan_runs_1(SearchShared& sh, int nnorm, int
 #pragma unroll
     for (int i = 0; i < PPT; ++i) {
         const int t = tid * ppt + i;
-        if (i < ppt && t < nnorm) sum += rb[i] - ra[i];
+        if (i < ppt && t < nnorm) sum += group_len(ra[i], rb[i]);
     }
     uint32_t incl = sum;
 #pragma unroll
@@ -202,9 +213,9 @@ __device__ __forceinline__ void scan_runs_2(SearchShared& sh, int buf, int nnorm
     for (int i = 0; i < PPT; ++i) {
         const int t = tid * ppt + i;
         if (i < ppt && t < nnorm) {
-            const uint32_t len = rb[i] - ra[i];
+            const uint32_t len = group_len(ra[i], rb[i]);
             sh.pre[buf][t] = run;
-            sh.rs[buf][t] = ra[i];
+            sh.rs[buf][t] = group_start(ra[i]);
             if (len)   // warps whose share starts inside this run
                 for (uint32_t w = (run + per - 1) / per; w * per < run + len && w < (uint32_t)nwarps; ++w)
                     sh.wli[buf][w] = (uint16_t)t;
@@ -431,8 +442,12 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 384 ? 2 : 1) search_kernel
         auto visit = [&](uint32_t c, uint32_t pid) {
             const uint32_t nn = (c >> kNbShift) + ((c >> kNyShift) & 63u);
             if (nn + (uint32_t)nslices < min_shared) return;
-            for (int s = 0; s < nslices; ++s)
-                if ((__ldg(sh.slice[s] + (pid >> 5)) >> (pid & 31)) & 1u) c += sh.slice_inc[s];
+            uint32_t hw[kMaxHot];   // every slice's word in flight at once
+#pragma unroll
+            for (int s = 0; s < kMaxHot; ++s) hw[s] = s < nslices ? __ldg(sh.slice[s] + (pid >> 5)) : 0u;
+#pragma unroll
+            for (int s = 0; s < kMaxHot; ++s)
+                if ((hw[s] >> (pid & 31)) & 1u) c += sh.slice_inc[s];
             score(c, pid);
         };
 
@@ -513,15 +528,17 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 384 ? 2 : 1) search_kernel
         // ---- a super-chunk in passes (see the header); entries of parity
         // buffer buf, peptide ids [x0, x1) of the span starting at cb
         // Pass A over the entries of parity buffer buf (the walk of
-        // for_each_entry, specialised): per batch of kJ entries a lane first
-        // issues all its loads, then all its seen-plane atomics, then the
-        // twice-plane atomics of the second hits, so the latencies overlap.
+        // for_each_entry, specialised to groups): lane l of a warp takes the
+        // 4-entry groups starting at f0 + 4 l + 128 j, each one 16-byte load,
+        // kG groups in flight before any is used; then per entry the
+        // seen-plane atomic, one 16-byte store of the group's 4 log records,
+        // and the twice-plane atomics of second hits, so latencies overlap.
         // A log record is (entry - 2 cb) | peak << 19, i.e. offset << 1 |
-        // isY in bits 0..18.
+        // isY in bits 0..18; entries outside [x0, x1) log 0xffffffff.
         auto pass_a = [&](int buf, uint32_t cb, uint32_t x0, uint32_t x1, int par) {
-            constexpr int kJ = 8;
-            const uint32_t R = sh.pre[buf][nnorm];
-            const uint32_t per = warp_share<THREADS>(R);
+            constexpr int kG = 4;
+            const uint32_t R = sh.pre[buf][nnorm];                 // a multiple of 4
+            const uint32_t per = warp_share<THREADS>(R);           // a multiple of 4
             const uint32_t f0 = (uint32_t)warp * per, f1 = min(R, f0 + per);
             uint32_t fresh = 0;   // twice bits this lane set first
             if (f0 < f1) {
@@ -529,14 +546,17 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 384 ? 2 : 1) search_kernel
                 uint32_t nxt = sh.pre[buf][li + 1];
                 const uint32_t* gp = a.entry + (sh.pbase[li] + sh.rs[buf][li] - sh.pre[buf][li]);
                 uint32_t lsh = (uint32_t)li << 19;
-                const uint32_t e_lo = x0 << 1, e_hi = x1 << 1, e_cb = cb << 1;   // entries of pids in [x0, x1)
-                for (uint32_t fb = f0 + lane; fb < f1; fb += 32 * kJ) {
-                    uint32_t ev[kJ], lr[kJ];
+                // entries of pids in [x0, x1): e - e_lo < e_span (unsigned)
+                const uint32_t e_lo = x0 << 1, e_span = (x1 - x0) << 1, e_cb = cb << 1;
+                uint4* const log4 = reinterpret_cast<uint4*>(logw);
+                for (uint32_t fb = f0 + 4u * lane; fb < f1; fb += 128u * kG) {
+                    uint4 ev[kG];
+                    uint32_t lr[kG];
 #pragma unroll
-                    for (int j = 0; j < kJ; ++j) {
-                        const uint32_t f = fb + 32 * j;
-                        ev[j] = 0xffffffffu;   // above e_hi: out of range
-                        lr[j] = 0u;
+                    for (int g = 0; g < kG; ++g) {
+                        const uint32_t f = fb + 128u * g;
+                        ev[g] = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
+                        lr[g] = 0u;
                         if (f < f1) {
                             while (f >= nxt) {
                                 ++li;
@@ -544,25 +564,29 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 384 ? 2 : 1) search_kernel
                                 gp = a.entry + (sh.pbase[li] + sh.rs[buf][li] - sh.pre[buf][li]);
                                 lsh = (uint32_t)li << 19;
                             }
-                            lr[j] = lsh;
-                            ev[j] = __ldg(gp + f);
+                            lr[g] = lsh;
+                            ev[g] = __ldg(reinterpret_cast<const uint4*>(gp + f));   // 16-byte aligned
                         }
                     }
-                    uint32_t old[kJ], bitv[kJ], wd[kJ];
 #pragma unroll
-                    for (int j = 0; j < kJ; ++j) {
-                        const bool in = ev[j] >= e_lo && ev[j] < e_hi;
-                        const uint32_t o2 = ev[j] - e_cb;
-                        const uint32_t off = o2 >> 1;
-                        bitv[j] = in ? 1u << (off & 31) : 0u;
-                        wd[j] = off >> 5;
-                        old[j] = in ? atomicOr(&seen[wd[j]], bitv[j]) : 0u;
-                        const uint32_t f = fb + 32 * j;
-                        if (f < f1) logw[f] = in ? (o2 | lr[j]) : 0xffffffffu;
+                    for (int g = 0; g < kG; ++g) {
+                        const uint32_t f = fb + 128u * g;
+                        const uint32_t e4[4] = {ev[g].x, ev[g].y, ev[g].z, ev[g].w};
+                        uint32_t rec[4], old[4], bitv[4], wd[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const bool in = e4[i] - e_lo < e_span;
+                            const uint32_t o2 = e4[i] - e_cb;
+                            bitv[i] = in ? __funnelshift_l(0u, 1u, o2 >> 1) : 0u;   // 1 << (offset & 31)
+                            wd[i] = o2 >> 6;
+                            old[i] = in ? atomicOr(&seen[wd[i]], bitv[i]) : 0u;
+                            rec[i] = in ? (o2 | lr[g]) : 0xffffffffu;
+                        }
+                        if (f < f1) log4[f >> 2] = make_uint4(rec[0], rec[1], rec[2], rec[3]);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            if (old[i] & bitv[i]) fresh += (atomicOr(&twice[wd[i]], bitv[i]) & bitv[i]) ? 0u : 1u;
                     }
-#pragma unroll
-                    for (int j = 0; j < kJ; ++j)
-                        if (old[j] & bitv[j]) fresh += (atomicOr(&twice[wd[j]], bitv[j]) & bitv[j]) ? 0u : 1u;
                 }
             }
 #pragma unroll
@@ -578,34 +602,52 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 384 ? 2 : 1) search_kernel
             const uint32_t g0 = (uint32_t)warp * G / nwarps, g1 = (uint32_t)(warp + 1) * G / nwarps;
             const uint32_t wbeg = g0 << 5, wpw = (g1 - g0) << 5;
             uint32_t mine = 0;
-            for (uint32_t i = lane; i < wpw; i += 32) {
+            // lane l takes the 4 words wbeg + 4 l + 128 j: 16-byte plane
+            // reads, and one 16-byte bitmap read per hot slice, all slices'
+            // reads in flight together
+            const uint32_t need = min_shared - 1;   // <= nslices <= kMaxHot when once_counts
+            for (uint32_t i = 4u * lane; i < wpw; i += 128u) {
                 const uint32_t w = wbeg + i;
-                const uint32_t s1 = seen[w];
-                uint32_t c2 = twice[w];
-                if (s1) {
-                    seen[w] = 0u;
+                const uint4 s4 = *reinterpret_cast<const uint4*>(seen + w);
+                uint4 c4 = *reinterpret_cast<const uint4*>(twice + w);
+                if (s4.x | s4.y | s4.z | s4.w) {
+                    *reinterpret_cast<uint4*>(seen + w) = make_uint4(0u, 0u, 0u, 0u);
                     if (once_counts) {
-                        uint32_t b1 = 0, b2 = 0, b3 = 0;   // hot-bit count per peptide: b3 marks 4 or more
-                        for (int s = 0; s < nslices; ++s) {
-                            const uint32_t h = __ldg(sh.slice[s] + (cb >> 5) + w);
-                            const uint32_t k1 = b1 & h;
-                            b1 ^= h;
-                            const uint32_t k2 = b2 & k1;
-                            b2 ^= k1;
-                            b3 |= k2;
-                        }
-                        const uint32_t need = min_shared - 1;   // <= nslices <= kMaxHot
-                        uint32_t enough;
-                        if (need == 0) enough = 0xffffffffu;
-                        else if (need == 1) enough = b1 | b2 | b3;
-                        else if (need == 2) enough = b2 | b3;
-                        else if (need == 3) enough = (b2 & b1) | b3;
-                        else enough = b3;                        // a superset: visit() is exact
-                        c2 |= s1 & enough;
-                        twice[w] = c2;
+                        uint4 h[kMaxHot];
+#pragma unroll
+                        for (int sl = 0; sl < kMaxHot; ++sl)
+                            h[sl] = sl < nslices ? __ldg(reinterpret_cast<const uint4*>(sh.slice[sl] + (cb >> 5) + w))
+                                                 : make_uint4(0u, 0u, 0u, 0u);
+                        // per peptide, peptides seen once with at least need
+                        // hot bits (b1, b2: the count's two low bits, b3: 4 or
+                        // more; a superset when need >= 4: visit() is exact)
+                        auto enough = [&](uint32_t s1, uint32_t c2, auto pick) {
+                            uint32_t b1 = 0, b2 = 0, b3 = 0;
+#pragma unroll
+                            for (int sl = 0; sl < kMaxHot; ++sl) {
+                                const uint32_t hh = pick(h[sl]);
+                                const uint32_t k1 = b1 & hh;
+                                b1 ^= hh;
+                                const uint32_t k2 = b2 & k1;
+                                b2 ^= k1;
+                                b3 |= k2;
+                            }
+                            uint32_t e;
+                            if (need == 0) e = 0xffffffffu;
+                            else if (need == 1) e = b1 | b2 | b3;
+                            else if (need == 2) e = b2 | b3;
+                            else if (need == 3) e = (b2 & b1) | b3;
+                            else e = b3;
+                            return c2 | (s1 & e);
+                        };
+                        c4.x = enough(s4.x, c4.x, [](const uint4& v) { return v.x; });
+                        c4.y = enough(s4.y, c4.y, [](const uint4& v) { return v.y; });
+                        c4.z = enough(s4.z, c4.z, [](const uint4& v) { return v.z; });
+                        c4.w = enough(s4.w, c4.w, [](const uint4& v) { return v.w; });
+                        *reinterpret_cast<uint4*>(twice + w) = c4;
                     }
                 }
-                mine += __popc(c2);
+                mine += __popc(c4.x) + __popc(c4.y) + __popc(c4.z) + __popc(c4.w);
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
