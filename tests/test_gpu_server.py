@@ -9,6 +9,8 @@ import pytest
 from paper_2102_02286_gb300 import configs, synth
 from paper_2102_02286_gb300 import hicops as hc
 
+from parity import assert_parity
+
 pytestmark = pytest.mark.gpu
 
 
@@ -55,6 +57,40 @@ def test_identity_alone_vs_mix(setup):
     assert st.completed == len(reqs) and st.spectra == spec.n
     assert st.launches < len(reqs)          # requests were packed together
     srv.close()
+
+
+def test_packed_requests_match_the_oracle(setup, oracle_lib):
+    """The server's own work (requests packed into shared launches, each
+    request's spectrum indices rebased, its histogram rows sliced out)
+    against the oracle, on a mix of +-10 / +-500 Da windows and 50-500 peaks:
+    parity per request."""
+    w, idx, spec = setup
+    assert set(np.unique(spec.tol_da)) == {10.0, 500.0}
+    npk = np.diff(spec.peak_off.astype(np.int64))
+    assert npk.min() < 100 and npk.max() > 400
+    rng = np.random.default_rng(7)
+    reqs = split_requests(spec.n, rng, max_size=96)
+    srv = hc.Server(idx, n_slots=3, slot_spectra=256)
+    tickets = [srv.submit(spec.subset(range(a, b))) for a, b in reqs]
+    got = [srv.poll(t, timeout_ms=120000) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    assert st.completed == len(reqs) and st.launches < len(reqs)   # packed
+    # the oracle (all pairs, +-500 Da windows of a 0.7M-entry database) on
+    # each request's first and last spectrum and on the most peaks of each
+    # window class
+    sel = {a for a, _ in reqs} | {b - 1 for _, b in reqs}
+    sel |= {int(np.flatnonzero(spec.tol_da == t)[np.argmax(npk[spec.tol_da == t])]) for t in (10.0, 500.0)}
+    sel = np.array(sorted(sel), dtype=np.uint32)
+    prot = synth.make_proteome(w.n_proteins, w.seed)
+    db = oracle_lib.OracleDb(prot.seq, prot.off, w.mods, w.params)
+    ref = db.search(spec, sel=sel)
+    rows = 0
+    for (a, b), g in zip(reqs, got):
+        pos = np.flatnonzero((sel >= a) & (sel < b))
+        r = oracle_lib.SearchResult(ref.psm[pos], ref.hist[pos], ref.n_scored[pos], ref.lo[pos], ref.hi[pos])
+        rows += assert_parity(g, r, sel=sel[pos] - a, label=f"request [{a}, {b})")
+    assert rows > len(sel)
 
 
 def test_concurrent_submitters(setup):
