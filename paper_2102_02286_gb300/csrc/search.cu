@@ -70,6 +70,8 @@ struct Workspace {
     uint64_t *seg_off = nullptr, *stmp = nullptr;
     UnitTop* utop = nullptr;
     unsigned long long* work = nullptr;
+    uint32_t* order = nullptr;   // [cap_n * max_seg] units, longest first
+    uint32_t* ocnt = nullptr;    // [2 * kOrderBuckets] bucket counts and starts
     hicops_psm* psm = nullptr;   // used when the caller gives no device output
     uint32_t* hist = nullptr;
     uint32_t* ns = nullptr;
@@ -90,6 +92,8 @@ hicops_status alloc_workspace(A& al, const hicops_params& p, uint32_t cap_n, uin
     HC_CUDA(al.get(&w.stmp, scan_tmp_words(cap_n)));
     HC_CUDA(al.get(&w.utop, (uint64_t)cap_n * max_seg * p.top_k));
     HC_CUDA(al.get(&w.work, 1));
+    HC_CUDA(al.get(&w.order, (uint64_t)cap_n * max_seg));
+    HC_CUDA(al.get(&w.ocnt, 2 * kOrderBuckets));
     if (outputs) {
         HC_CUDA(al.get(&w.psm, (uint64_t)cap_n * p.top_k));
         HC_CUDA(al.get(&w.hist, (uint64_t)cap_n * kHistBins));
@@ -121,11 +125,12 @@ hicops_status check_config(const hicops_search_config& c) {
 }
 
 // Default shape: 384-thread CTAs (two fit an SM while the top-k lists are
-// at most 16 long), else 256.
+// at most 16 long), else 256; super-chunks of about 6 k entries (the
+// autotuner's choice on the open-search workloads).
 hicops_search_config resolved(const hicops_search_config& c, uint32_t k) {
     hicops_search_config r = c;
     if (!r.threads) r.threads = k <= 16 ? 384 : 256;
-    if (!r.chunk_entries) r.chunk_entries = 2;
+    if (!r.chunk_entries) r.chunk_entries = 6;
     return r;
 }
 
@@ -221,13 +226,20 @@ hicops_status enqueue_search(hicops_index* idx, const DevBatch& d, uint32_t n, c
     count_launches(1);
     HC_CUDA(cudaGetLastError());
     HC_CUDA(exclusive_scan<uint32_t>(w.nseg, n, w.seg_off, w.seg_off + n, w.stmp, s));
+    HC_CUDA(cudaMemsetAsync(w.ocnt, 0, sizeof(uint32_t) * kOrderBuckets, s));
+    order_count_kernel<<<(n + 255) / 256, 256, 0, s>>>(w.qn, w.lo, w.hi, w.seg_off, n, w.ocnt);
+    order_scan_kernel<<<1, 32, 0, s>>>(w.ocnt);
+    order_scatter_kernel<<<(n + 255) / 256, 256, 0, s>>>(w.qn, w.lo, w.hi, w.seg_off, n, w.ocnt + kOrderBuckets,
+                                                         w.order);
+    count_launches(3);
+    HC_CUDA(cudaGetLastError());
     HC_CUDA(cudaMemsetAsync(d_hist, 0, sizeof(uint32_t) * n * kHistBins, s));
     HC_CUDA(cudaMemsetAsync(d_ns, 0, sizeof(uint32_t) * n, s));
     HC_CUDA(cudaMemsetAsync(w.work, 0, sizeof(unsigned long long), s));
     SearchArgs sa{w.qbin, w.qiq, w.qn, w.lo, w.hi, w.seg_off, n, query_bins_cap(p), di.off, di.entry,
                   di.skip_row, di.skip, di.skip_stride, di.hot_id, di.hot_b, di.hot_y, di.hot_flags,
                   di.hot_words, di.lf, di.ls, (uint32_t)idx->s_max, p.min_shared, k, cfg.chunk_entries * 1024u, w.utop, d_hist, d_ns,
-                  w.work};
+                  w.work, w.order};
     mark(idx, 2, s, timing_marks);
     st = launch_search(sa, cfg, (uint64_t)n * max_seg, s);
     if (st != HICOPS_OK) return st;
@@ -472,7 +484,7 @@ extern "C" hicops_status hicops_autotune(hicops_index* idx, const hicops_batch* 
     if (st != HICOPS_OK) return st;
     if (!b->on_device || b->n == 0) { set_error("autotune needs a non-empty device batch"); return HICOPS_EINVAL; }
     const uint32_t cand_threads[2] = {256, 384};
-    const uint32_t cand_cm[4] = {3, 4, 5, 6};   // chunk_entries
+    const uint32_t cand_cm[5] = {2, 3, 4, 5, 6};   // chunk_entries
     const uint32_t cand_ctas[2] = {0, 1};
     const uint32_t cand_seg[3] = {0, 1u << 18, 1u << 16};
     cudaStream_t s = (cudaStream_t)b->cuda_stream;
@@ -573,6 +585,8 @@ constexpr uint64_t noalloc_bytes(uint64_t cap) {
            + 4096                                                // scan temporaries
            + align256(sizeof(UnitTop) * cap * kNoAllocSegs * kMaxTopK)
            + 256                                                 // work counter
+           + align256(4 * cap * kNoAllocSegs)                    // unit order
+           + align256(4 * 2 * kOrderBuckets)                     // its bucket counts
            + align256(sizeof(hicops_psm) * cap * kMaxTopK)       // psm (unused here)
            + align256(4 * cap * kHistBins) + align256(4 * cap);  // hist, n_scored
 }

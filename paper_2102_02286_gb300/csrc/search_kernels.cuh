@@ -266,6 +266,79 @@ __global__ void plan_kernel(const uint32_t* __restrict__ qn, const uint32_t* __r
     nseg[q] = s;
 }
 
+// ---- unit order: longest first (the persistent CTAs take units in this
+// order, so the short ones fill the end of the launch).  A unit's cost is
+// estimated as its peptide range times the spectrum's retained peaks; units
+// are bucketed by the cost's binary magnitude (a counting sort over 64
+// buckets, descending), block histograms first so that the global atomics
+// stay few.
+constexpr int kOrderBuckets = 64;
+
+__device__ __forceinline__ int order_bucket(const uint32_t* qn, const uint32_t* lo, const uint32_t* hi,
+                                            const uint64_t* seg_off, uint32_t q, uint32_t* ns) {
+    *ns = (uint32_t)(seg_off[q + 1] - seg_off[q]);
+    if (*ns == 0) return 0;
+    const uint64_t W = hi[q] - lo[q];
+    const uint64_t cost = ((W + *ns - 1) / *ns) * (uint64_t)(qn[q] ? qn[q] : 1) + 1;
+    return __clzll((long long)cost);   // 0 for the costliest magnitudes: descending order
+}
+
+__global__ void order_count_kernel(const uint32_t* __restrict__ qn, const uint32_t* __restrict__ lo,
+                                   const uint32_t* __restrict__ hi, const uint64_t* __restrict__ seg_off,
+                                   uint32_t n, uint32_t* __restrict__ cnt) {
+    __shared__ uint32_t bc[kOrderBuckets];
+    for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x) bc[i] = 0;
+    __syncthreads();
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) {
+        uint32_t ns;
+        const int b = order_bucket(qn, lo, hi, seg_off, q, &ns);
+        if (ns) atomicAdd(&bc[b], ns);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x)
+        if (bc[i]) atomicAdd(&cnt[i], bc[i]);
+}
+
+// cnt[0..63] counts -> cnt[64..127] exclusive starts (one warp)
+__global__ void order_scan_kernel(uint32_t* __restrict__ cnt) {
+    const int lane = threadIdx.x;
+    const uint32_t a = cnt[lane], b = cnt[32 + lane];
+    uint32_t ia = a, ib = b;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t xa = __shfl_up_sync(0xffffffffu, ia, o), xb = __shfl_up_sync(0xffffffffu, ib, o);
+        if (lane >= o) { ia += xa; ib += xb; }
+    }
+    const uint32_t tot_a = __shfl_sync(0xffffffffu, ia, 31);
+    cnt[kOrderBuckets + lane] = ia - a;
+    cnt[kOrderBuckets + 32 + lane] = tot_a + ib - b;
+}
+
+__global__ void order_scatter_kernel(const uint32_t* __restrict__ qn, const uint32_t* __restrict__ lo,
+                                     const uint32_t* __restrict__ hi, const uint64_t* __restrict__ seg_off,
+                                     uint32_t n, uint32_t* __restrict__ cursor, uint32_t* __restrict__ order) {
+    __shared__ uint32_t bc[kOrderBuckets], bb[kOrderBuckets];
+    for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x) bc[i] = 0;
+    __syncthreads();
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t ns = 0, local = 0;
+    int b = 0;
+    if (q < n) {
+        b = order_bucket(qn, lo, hi, seg_off, q, &ns);
+        if (ns) local = atomicAdd(&bc[b], ns);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x)
+        if (bc[i]) bb[i] = atomicAdd(&cursor[i], bc[i]);
+    __syncthreads();
+    if (ns) {
+        const uint32_t pos = bb[b] + local;
+        const uint64_t u0 = seg_off[q];
+        for (uint32_t s = 0; s < ns; ++s) order[pos + s] = (uint32_t)(u0 + s);
+    }
+}
+
 #include "search_kernel.cuh"
 
 // lower bound of pid key (pid << 1) in entry[a, b)
