@@ -67,6 +67,13 @@ def parse():
     ap.add_argument("--load-spectra", type=int, default=300000, help="serving: cap on spectra per load")
     ap.add_argument("--shape", default="", help="fixed launch shape threads,chunk_entries,ctas_per_sm,seg_pids "
                                                 "(skips the autotuner)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="step mode: skip the sub-records (open_large step, uneven batch, serving loads)")
+    ap.add_argument("--extra-large-spectra", type=int, default=20000, help="extras: open_large spectra per step")
+    ap.add_argument("--extra-batched-spectra", type=int, default=100000, help="extras: uneven-batch spectra")
+    ap.add_argument("--extra-loads", default="20000,100000,1000000", help="extras: serving offered loads")
+    ap.add_argument("--extra-load-seconds", type=float, default=1.5, help="extras: serving arrival window")
+    ap.add_argument("--extra-pool", type=int, default=20000, help="extras: serving spectrum pool")
     return ap.parse_args()
 
 
@@ -232,11 +239,102 @@ def spectrum_classes(spec, n_deciles=10):
     return [np.flatnonzero(cls == c) for c in range(len(tols) * n_deciles) if np.any(cls == c)]
 
 
+def timed_steps(torch, stream, flush, fn, warmup, steps):
+    """CUDA-event milliseconds of each of `steps` calls of fn after `warmup`
+    untimed ones, L2 flushed before each timed call."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    return ms
+
+
+def batched_record(args, hc, torch, idx, spec, w, warmup, steps):
+    """The batched form against plain per-class launches, both with the same
+    autotuned launch shape (so the batching gain is not a shape gain), plus
+    the per-class launches with the library's default shape and one launch
+    without the graph; results of every form must be identical."""
+    n, k = spec.n, w.params.top_k
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
+    groups = spectrum_classes(spec)
+    sub = [spec.subset(g) for g in groups]
+    dbs = [hc.DeviceBatch.from_spectra(x) for x in sub]
+    outs = [hc.DeviceResult.alloc(x.n, k) for x in sub]
+    db_all = hc.DeviceBatch.from_spectra(spec)
+    out_all = hc.DeviceResult.alloc(n, k)
+    med = lambda fn: statistics.median(timed_steps(torch, stream, flush, fn, warmup, steps))  # noqa: E731
+
+    t0 = time.perf_counter()
+    tune = hc.DeviceBatch.from_spectra(spec.subset(np.arange(min(n, args.tune_spectra or 20000))))
+    shape, _ = idx.autotune(tune)
+    t_tune = time.perf_counter() - t0
+    del tune
+    sampler = ClockSampler(0)
+    sampler.start()
+    # plain per-class launches: the library's default shape, then the tuned one
+    idx.set_config(None)
+    per_class_default_ms = med(lambda: [idx.search_device(d, o, stream) for d, o in zip(dbs, outs)])
+    idx.set_config(shape)
+    launches0 = hc.kernel_launches()
+    per_class_ms = med(lambda: [idx.search_device(d, o, stream) for d, o in zip(dbs, outs)])
+    per_class_launches = (hc.kernel_launches() - launches0) // (warmup + steps)
+    per_class_res = [o.to_host(x.n, k) for o, x in zip(outs, sub)]
+    # one launch over the whole batch, tuned shape, no graph
+    plan0 = idx.plan(n, shape)
+    one_ms = med(lambda: plan0.search(db_all, out_all, stream, graph=False))
+    plan0.close()
+    # one launch, tuned shape, captured once and replayed as a CUDA graph
+    plan = idx.plan(n, shape)
+    plan.search(db_all, out_all, stream, graph=True)     # capture
+    torch.cuda.synchronize()
+    launches0 = hc.kernel_launches()
+    batched_ms = med(lambda: plan.search(db_all, out_all, stream, graph=True))
+    batched_launches = (hc.kernel_launches() - launches0) // (warmup + steps)
+    clocks = sampler.stop()
+    got = out_all.to_host(n, k)
+    identical = True
+    for g, r, x in zip(groups, per_class_res, sub):
+        exp = got.psm[g].copy()
+        exp["query"] = np.arange(x.n)[:, None]
+        identical &= bool(np.array_equal(r.psm, exp) and np.array_equal(r.hist, got.hist[g])
+                          and np.array_equal(r.n_scored, got.n_scored[g]))
+    plan.close()
+    npk = np.diff(spec.peak_off.astype(np.int64))
+    return {
+        "workload": workload_desc(w), "spectra": n,
+        "peaks_per_spectrum": [int(npk.min()), int(npk.max())],
+        "tolerances_da": sorted(set(float(t) for t in spec.tol_da)),
+        "launch_shape": shape.as_dict(), "autotune_s": t_tune,
+        "l2": "L2 flushed (256 MB write) before every timed step",
+        "batched": {"spectra_per_s": n / (batched_ms / 1000.0), "ms_per_step": batched_ms,
+                    "gpu_launches_per_step": int(batched_launches),
+                    "what": "one persistent launch over the whole batch, tuned shape, CUDA graph replay"},
+        "per_class_tuned": {"spectra_per_s": n / (per_class_ms / 1000.0), "ms_per_step": per_class_ms,
+                            "classes": len(groups), "gpu_launches_per_step": int(per_class_launches),
+                            "what": "one hicops_search per (tolerance class x peak-count decile), same tuned "
+                                    "shape, stream-ordered scratch per call"},
+        "per_class_default_shape": {"spectra_per_s": n / (per_class_default_ms / 1000.0),
+                                    "ms_per_step": per_class_default_ms},
+        "one_launch_no_graph": {"spectra_per_s": n / (one_ms / 1000.0), "ms_per_step": one_ms},
+        "speedup_vs_per_class": per_class_ms / batched_ms,
+        "identical_results": identical,
+        "clocks": clocks,
+    }
+
+
 def run_batched(args):
     """Batched form: the whole uneven batch in one persistent launch with the
     autotuned shape, replayed as a CUDA graph, against one plain hicops_search
-    launch per spectrum class with the default shape; results must be
-    identical."""
+    launch per spectrum class with the same shape; results must be identical."""
     import torch
     from paper_2102_02286_gb300 import build as pkg_build
     from paper_2102_02286_gb300 import hicops as hc
@@ -250,91 +348,24 @@ def run_batched(args):
     prot = synth.make_proteome(w.n_proteins, w.db_seed, w.protein_len)
     spec = synth.make_spectra(prot, w)
     idx = hc.Index(prot.seq, prot.off, w.mods, w.params)
-    n, k = spec.n, w.params.top_k
-    stream = torch.cuda.current_stream()
-    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
-
-    groups = spectrum_classes(spec)
-    sub = [spec.subset(g) for g in groups]
-    dbs = [hc.DeviceBatch.from_spectra(x) for x in sub]
-    outs = [hc.DeviceResult.alloc(x.n, k) for x in sub]
-    db_all = hc.DeviceBatch.from_spectra(spec)
-    out_all = hc.DeviceResult.alloc(n, k)
-
-    def timed(fn):
-        for _ in range(args.warmup):
-            fn()
-        torch.cuda.synchronize()
-        ms = []
-        for _ in range(args.steps):
-            flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            fn()
-            b.record(stream)
-            b.synchronize()
-            ms.append(a.elapsed_time(b))
-        return statistics.median(ms)
-
-    # plain per-class launches, default shape
-    idx.set_config(None)
-    launches0 = hc.kernel_launches()
-    per_class_ms = timed(lambda: [idx.search_device(d, o, stream) for d, o in zip(dbs, outs)])
-    per_class_launches = (hc.kernel_launches() - launches0) // (args.warmup + args.steps)
-    # one launch, default shape, no graph
-    plan0 = idx.plan(n, hc.SearchConfig())
-    one_default_ms = timed(lambda: plan0.search(db_all, out_all, stream, graph=False))
-    plan0.close()
-    # one launch, autotuned shape, captured once and replayed as a CUDA graph
-    t0 = time.perf_counter()
-    tune = hc.DeviceBatch.from_spectra(spec.subset(np.arange(min(n, args.tune_spectra or 20000))))
-    shape, _ = idx.autotune(tune)
-    t_tune = time.perf_counter() - t0
-    del tune
-    plan = idx.plan(n, shape)
-    plan.search(db_all, out_all, stream, graph=True)     # capture
-    torch.cuda.synchronize()
-    launches0 = hc.kernel_launches()
-    batched_ms = timed(lambda: plan.search(db_all, out_all, stream, graph=True))
-    batched_launches = (hc.kernel_launches() - launches0) // (args.warmup + args.steps)
-
-    # identical results: every class's rows against the same spectra's rows of the one launch
-    got = out_all.to_host(n, k)
-    identical = True
-    for g, o, x in zip(groups, outs, sub):
-        r = o.to_host(x.n, k)
-        exp = got.psm[g].copy()
-        exp["query"] = np.arange(x.n)[:, None]
-        identical &= bool(np.array_equal(r.psm, exp) and np.array_equal(r.hist, got.hist[g])
-                          and np.array_equal(r.n_scored, got.n_scored[g]))
-    plan.close()
+    rec = batched_record(args, hc, torch, idx, spec, w, args.warmup, args.steps)
     idx.close()
-    npk = np.diff(spec.peak_off.astype(np.int64))
     line = {
         "metric": "spectra/s, uneven batch: one autotuned persistent launch replayed as a CUDA graph",
-        "value": n / (batched_ms / 1000.0),
-        "unit": "spectra/s",
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": batched_ms,
+        "value": rec["batched"]["spectra_per_s"], "unit": "spectra/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": rec["batched"]["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": workload_desc(w), "spectra_per_step": n,
-                   "peaks_per_spectrum": [int(npk.min()), int(npk.max())],
-                   "tolerances_da": sorted(set(float(t) for t in spec.tol_da)),
-                   "l2": "L2 flushed (256 MB write) before every timed step",
-                   "launch_shape": shape.as_dict(), "autotune_s": t_tune},
-        "baselines": {
-            "per_class_default": {"spectra_per_s": n / (per_class_ms / 1000.0), "ms_per_step": per_class_ms,
-                                  "classes": len(groups), "gpu_launches_per_step": int(per_class_launches),
-                                  "what": "one hicops_search per (tolerance class x peak-count decile), "
-                                          "default shape, stream-ordered scratch per call"},
-            "one_launch_default": {"spectra_per_s": n / (one_default_ms / 1000.0), "ms_per_step": one_default_ms,
-                                   "what": "one plan launch over the whole batch, default shape, no graph"},
-        },
-        "speedup_vs_per_class": per_class_ms / batched_ms,
-        "identical_results": identical,
-        "gpu_launches": int(batched_launches),
+        "config": {"workload": rec["workload"], "spectra_per_step": rec["spectra"],
+                   "peaks_per_spectrum": rec["peaks_per_spectrum"], "tolerances_da": rec["tolerances_da"],
+                   "l2": rec["l2"], "launch_shape": rec["launch_shape"], "autotune_s": rec["autotune_s"]},
+        "baselines": {k: rec[k] for k in ("per_class_tuned", "per_class_default_shape", "one_launch_no_graph")},
+        "speedup_vs_per_class": rec["speedup_vs_per_class"],
+        "identical_results": rec["identical_results"],
+        "gpu_launches": rec["batched"]["gpu_launches_per_step"],
+        "clocks": rec["clocks"],
     }
     print(json.dumps(line), flush=True)
-    return 0 if identical else 1
+    return 0 if rec["identical_results"] else 1
 
 
 def poisson_requests(rng, offered, seconds, cap_spectra, pool_n, max_batch=4096):
@@ -398,6 +429,45 @@ def serve_stream(idx, hc, reqs, batches, server):
     return np.array(lat), end - t0, res
 
 
+def serving_loads(hc, idx, pool, w, loads, seconds, cap_spectra):
+    """Per offered load: a Poisson request stream replayed in real time
+    through the server and through the plain one-batch-per-launch loop;
+    sustained spectra/s, p50/p99 latency, identical results per request."""
+    rng = np.random.default_rng(w.seed + 17)
+    # warm-up: both paths once on a small request
+    warm = pool.subset(np.arange(min(64, pool.n)))
+    idx.search(warm)
+    server = hc.Server(idx)
+    server.poll(server.submit(warm), -1)
+    sstats0 = server.stats()
+    rows = []
+    identical = True
+    for offered in loads:
+        reqs = poisson_requests(rng, offered, seconds, cap_spectra, pool.n)
+        batches = request_batches(pool, reqs)
+        nspec = sum(r[2] for r in reqs)
+        sampler = ClockSampler(0)
+        sampler.start()
+        lat_s, span_s, res_s = serve_stream(idx, hc, reqs, batches, server)
+        lat_p, span_p, res_p = serve_stream(idx, hc, reqs, batches, None)
+        clocks = sampler.stop()
+        for a, b in zip(res_s, res_p):
+            identical &= bool(np.array_equal(a.psm, b.psm) and np.array_equal(a.hist, b.hist)
+                              and np.array_equal(a.n_scored, b.n_scored))
+        row = {"offered_spectra_per_s": offered, "requests": len(reqs), "spectra": int(nspec)}
+        for name, lat, span in (("server", lat_s, span_s), ("plain_loop", lat_p, span_p)):
+            row[name] = {"spectra_per_s": nspec / span, "p50_ms": 1000 * float(np.percentile(lat, 50)),
+                         "p99_ms": 1000 * float(np.percentile(lat, 99)),
+                         "saturated": bool(nspec / span < 0.9 * offered)}
+        row["throughput_ratio"] = row["server"]["spectra_per_s"] / row["plain_loop"]["spectra_per_s"]
+        row["clocks"] = clocks
+        rows.append(row)
+        print(json.dumps({"load": row}), file=sys.stderr, flush=True)
+    sstats = server.stats()
+    server.close()
+    return rows, identical, sstats, sstats.launches - sstats0.launches
+
+
 def run_serving(args):
     """Serving form: a Poisson stream of spectrum batches through the
     continuous-batching server, against a plain one-batch-per-launch loop;
@@ -421,35 +491,8 @@ def run_serving(args):
     idx = hc.Index(prot.seq, prot.off, w.mods, w.params)
     t_index = time.perf_counter() - t0
     st = idx.stats()
-    rng = np.random.default_rng(w.seed + 17)
-    # warm-up: both paths once on a small request
-    warm = pool.subset(np.arange(min(64, pool.n)))
-    idx.search(warm)
-    server = hc.Server(idx)
-    server.poll(server.submit(warm), -1)
-    sstats0 = server.stats()
     loads = [float(x) for x in args.loads.split(",") if x]
-    rows = []
-    identical = True
-    for offered in loads:
-        reqs = poisson_requests(rng, offered, args.load_seconds, args.load_spectra, pool.n)
-        batches = request_batches(pool, reqs)
-        nspec = sum(r[2] for r in reqs)
-        lat_s, span_s, res_s = serve_stream(idx, hc, reqs, batches, server)
-        lat_p, span_p, res_p = serve_stream(idx, hc, reqs, batches, None)
-        for a, b in zip(res_s, res_p):
-            identical &= bool(np.array_equal(a.psm, b.psm) and np.array_equal(a.hist, b.hist)
-                              and np.array_equal(a.n_scored, b.n_scored))
-        row = {"offered_spectra_per_s": offered, "requests": len(reqs), "spectra": int(nspec)}
-        for name, lat, span in (("server", lat_s, span_s), ("plain_loop", lat_p, span_p)):
-            row[name] = {"spectra_per_s": nspec / span, "p50_ms": 1000 * float(np.percentile(lat, 50)),
-                         "p99_ms": 1000 * float(np.percentile(lat, 99)),
-                         "saturated": bool(nspec / span < 0.9 * offered)}
-        row["throughput_ratio"] = row["server"]["spectra_per_s"] / row["plain_loop"]["spectra_per_s"]
-        rows.append(row)
-        print(json.dumps({"load": row}), file=sys.stderr, flush=True)
-    sstats = server.stats()
-    server.close()
+    rows, identical, sstats, launches = serving_loads(hc, idx, pool, w, loads, args.load_seconds, args.load_spectra)
     idx.close()
     best = max(rows, key=lambda r: r["server"]["spectra_per_s"])
     line = {
@@ -462,7 +505,7 @@ def run_serving(args):
                    "index_build_s": t_index, "input_gen_s": t_gen, "pool_spectra": pool.n,
                    "batch_sizes": "log-uniform in [1, 4096]", "arrival_window_s": args.load_seconds,
                    "server_slots": int(sstats.n_slots), "slot_bytes": int(sstats.slot_bytes),
-                   "server_launches": int(sstats.launches - sstats0.launches)},
+                   "server_launches": int(launches)},
         "loads": rows,
         "identical_results": identical,
     }
@@ -629,6 +672,91 @@ def run_ingest(args):
     }
     print(json.dumps(line), flush=True)
     return 0 if identical else 1
+
+
+def step_record(hc, torch, w, warmup, steps):
+    """A workload's search step (inputs resident, L2 flushed before every
+    timed step, default launch shape): spectra/s and the search kernel's
+    fraction of the HBM roofline, as for the headline line."""
+    t0 = time.perf_counter()
+    prot = synth.make_proteome(w.n_proteins, w.db_seed, w.protein_len)
+    spec = synth.make_spectra(prot, w)
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    idx = hc.Index(prot.seq, prot.off, w.mods, w.params)
+    t_index = time.perf_counter() - t0
+    st = idx.stats()
+    n, k = spec.n, w.params.top_k
+    lo, hi, npk, hits = idx.search_work(spec)
+    search_bytes = 4 * int(hits.sum()) + 24 * int(npk.sum()) + (16 * k + 4 * 256) * n
+    db = hc.DeviceBatch.from_spectra(spec)
+    out = hc.DeviceResult.alloc(n, k)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
+    idx.set_timing(True)
+    for _ in range(warmup):
+        idx.search_device(db, out, stream)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    step_ms, search_ms = [], []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        idx.search_device(db, out, stream)
+        b.record(stream)
+        search_ms.append(idx.last_timing().search_ms)
+        step_ms.append(a.elapsed_time(b))
+    clocks = sampler.stop()
+    idx.close()
+    peak, peak_src = measured_peaks()
+    achieved = search_bytes / (statistics.mean(search_ms) / 1000.0) / 1e9
+    return {"workload": workload_desc(w), "spectra_per_step": n, "n_peptides": int(st.n_peptides),
+            "n_index_entries": int(st.n_entries), "index_bytes": int(st.device_bytes),
+            "index_build_s": t_index, "input_gen_s": t_gen, "mean_hits_per_spectrum": float(hits.mean()),
+            "spectra_per_s": n * steps / (sum(step_ms) / 1000.0), "ms_per_step": statistics.mean(step_ms),
+            "search_ms": statistics.mean(search_ms), "launch_shape": "library default",
+            "l2": "L2 flushed (256 MB write) before every timed step",
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "kernel": "search_kernel", "bytes_per_launch": search_bytes,
+                         "peak_source": peak_src},
+            "clocks": clocks}
+
+
+def extras(args, hc, torch):
+    """Sub-records of the default run: config 2's step (open_large), the
+    batched form on config 3's uneven batch and the serving loop's loads on
+    config 4's index, each with the clocks sampled while it ran."""
+    out = {}
+    t0 = time.perf_counter()
+    w = configs.OPEN_LARGE.with_spectra(args.extra_large_spectra)
+    out["open_large"] = step_record(hc, torch, w, 2, 3)
+    out["open_large"]["wall_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    w = configs.UNEVEN_BATCHED.with_spectra(args.extra_batched_spectra)
+    prot = synth.make_proteome(w.n_proteins, w.db_seed, w.protein_len)
+    spec = synth.make_spectra(prot, w)
+    idx = hc.Index(prot.seq, prot.off, w.mods, w.params)
+    out["uneven_batched"] = batched_record(args, hc, torch, idx, spec, w, 3, 3)
+    idx.close()
+    del prot, spec
+    out["uneven_batched"]["wall_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    w = configs.SERVING_STREAM.with_spectra(args.extra_pool)
+    prot = synth.make_proteome(w.n_proteins, w.db_seed, w.protein_len)
+    pool = synth.make_spectra(prot, w)
+    idx = hc.Index(prot.seq, prot.off, w.mods, w.params)
+    loads = [float(x) for x in args.extra_loads.split(",") if x]
+    rows, identical, sstats, launches = serving_loads(hc, idx, pool, w, loads, args.extra_load_seconds,
+                                                      3 * args.extra_pool)
+    idx.close()
+    out["serving_stream"] = {"workload": workload_desc(w), "pool_spectra": pool.n,
+                             "batch_sizes": "log-uniform in [1, 4096]", "arrival_window_s": args.extra_load_seconds,
+                             "server_slots": int(sstats.n_slots), "server_launches": int(launches),
+                             "loads": rows, "identical_results": identical,
+                             "wall_s": time.perf_counter() - t0}
+    return out
 
 
 def main():
@@ -834,6 +962,9 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, prot, spec, args.oracle_spectra)
     idx.close()
+    if world == 1 and not args.no_extras and not args.config:
+        del dev_batch, out, flush
+        line["extras"] = extras(args, hc, torch)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
