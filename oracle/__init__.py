@@ -84,6 +84,8 @@ def lib():
         L.or_mod_distance.restype = C.c_double
         L.or_mod_distance.argtypes = [C.c_char_p, P, C.c_char_p, P]
         L.or_partition_lbe.argtypes = [P, C.c_uint32, P]
+        L.or_hist_sample.restype = C.c_uint32
+        L.or_hist_sample.argtypes = [P, C.c_uint32, C.c_uint32, P, P]
     return _lib
 
 
@@ -211,6 +213,26 @@ def evalue(hist, keys, pids, evalue_mode=0) -> np.ndarray:
     pids = np.ascontiguousarray(pids, np.uint32)
     out = np.zeros(len(keys), np.float64)
     lib().or_evalue(_ptr(hist), len(hist), _ptr(keys), _ptr(pids), len(keys), evalue_mode, _ptr(out))
+    return out
+
+
+def hist_sample(hist, s: int = 120):
+    """R19: (lo, len, mean) of the bins kept when the score distribution is
+    sampled down to at most s bins around its mean."""
+    hist = np.ascontiguousarray(hist, np.uint32)
+    lo = np.zeros(1, np.uint32)
+    ln = np.zeros(1, np.uint32)
+    m = lib().or_hist_sample(_ptr(hist), len(hist), s, _ptr(lo), _ptr(ln))
+    return int(lo[0]), int(ln[0]), int(m)
+
+
+def sampled(hist, s: int = 120) -> np.ndarray:
+    """The histogram as the receiver of its sample sees it: the kept bins'
+    counts, zero elsewhere."""
+    hist = np.asarray(hist, np.uint32)
+    lo, ln, _ = hist_sample(hist, s)
+    out = np.zeros_like(hist)
+    out[lo:lo + ln] = hist[lo:lo + ln]
     return out
 
 

@@ -68,14 +68,24 @@
 //      of -ln(-ln F_j) on x = j + 1, F_j = fraction scoring below j + 1, over
 //      bins with 0 < F_j < 1; e = N * (1 - exp(-exp(-(a x + c)))), x =
 //      K*2^-31; fewer than 3 points or a <= 0 -> e = N.
+//   R19 sampling of a partial score distribution (Sampling section and its
+//      figure): a sample is one histogram bin; the mean is the integer
+//      average (rounded down) of the locations of the three most intense
+//      bins (count descending, lower location first on equal counts; fewer
+//      when fewer bins are non-zero); from the non-zero support [L, R] the
+//      tail samples are pruned first: while more than s bins remain, the
+//      end farther from the mean is dropped (the upper end on a tie); the
+//      kept bins are one run [lo, lo + len) with their exact counts.
 //
 // Parity pins: see tests/test_oracle_pins.py (closed forms, elemental
 // composition masses, brute force on tiny inputs, invariants, library
 // routines, the Mod Distance worked example).  Parity unpinned: the absolute
 // scale of the hyperscore, the histogram bin width and the e-value fit
 // window (R10-R12), the smoothing window and order (R16), the log-Weibull
-// fitting method (R17) and the LBE cluster rule (R18) are readings with no
-// printed value.
+// fitting method (R17), the LBE cluster rule (R18) and the sampling's
+// rounding of the mean and tie rule (R19) are readings with no printed
+// value.  R19 is pinned by hand-worked distributions and by its result
+// stated as an optimisation (tests/golden/sampling_hand.txt).
 
 #include <cmath>
 #include <cstdint>
@@ -570,6 +580,35 @@ void or_evalue(const uint32_t* hist, uint32_t nbins, const int64_t* keys, const 
     std::vector<double> ev;
     evalues(hist, nbins, top, ev_mode, ev);
     for (uint32_t i = 0; i < k; ++i) out[i] = ev[i];
+}
+
+// R19: the bins [*lo, *lo + *len) of hist[0..nbins) kept when the
+// distribution is sampled down to at most s bins around its mean; *len = 0
+// for an empty histogram.  Returns the mean's location.
+uint32_t or_hist_sample(const uint32_t* hist, uint32_t nbins, uint32_t s, uint32_t* lo, uint32_t* len) {
+    *lo = 0;
+    *len = 0;
+    // the three most intense samples (count descending, location ascending)
+    std::vector<uint32_t> order;
+    for (uint32_t j = 0; j < nbins; ++j)
+        if (hist[j] > 0) order.push_back(j);
+    if (order.empty() || s == 0) return 0;
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return hist[a] > hist[b]; });
+    const size_t top = std::min<size_t>(3, order.size());
+    uint64_t sum = 0;
+    for (size_t i = 0; i < top; ++i) sum += order[i];
+    const uint32_t mean = (uint32_t)(sum / top);
+    // the support, then the tails pruned first
+    uint32_t a = nbins, b = 0;
+    for (uint32_t j = 0; j < nbins; ++j)
+        if (hist[j] > 0) { a = std::min(a, j); b = std::max(b, j); }
+    while (b - a + 1 > s) {
+        if (b - mean >= mean - a) --b;
+        else ++a;
+    }
+    *lo = a;
+    *len = b - a + 1;
+    return mean;
 }
 
 // Search the selected spectra (indices sel[0..n_sel-1] of the batch).

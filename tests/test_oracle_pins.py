@@ -789,3 +789,95 @@ def test_lbe_partition_balance_invariants(oracle_lib):
             c = len(members)
             assert sorted(per.tolist()) == sorted([c // n_parts + 1] * (c % n_parts) +
                                                   [c // n_parts] * (n_parts - c % n_parts))
+
+
+# ---------------------------------------------------------------- R19: sampling
+
+
+def _golden_samples():
+    with open(os.path.join(GOLDEN, "sampling_hand.txt")) as f:
+        rows = [l.split() for l in f if l.strip() and not l.startswith("#")]
+    for name, s, nbins, bins, mean, lo, ln in rows:
+        h = np.zeros(int(nbins), np.uint32)
+        if bins != "-":
+            for jc in bins.split(","):
+                j, c = jc.split(":")
+                h[int(j)] = int(c)
+        yield name, int(s), h, int(mean), int(lo), int(ln)
+
+
+def test_sampling_hand_worked(oracle_lib):
+    cases = list(_golden_samples())
+    assert len(cases) == 7
+    for name, s, h, mean, lo, ln in cases:
+        got = oracle_lib.hist_sample(h, s)
+        if ln:
+            assert got == (lo, ln, mean), name
+        else:
+            assert got[1] == 0, name
+
+
+def _window_by_definition(h, s):
+    """The kept run stated without the pruning loop: among the runs of at
+    most s bins inside the support that contain the mean, the shortest
+    longest-side run (max distance from the mean to an end), ties to the
+    lower run; the whole support when it has at most s bins."""
+    nz = np.flatnonzero(h)
+    if len(nz) == 0:
+        return None
+    order = np.lexsort((np.arange(len(h)), -h.astype(np.int64)))   # count desc, location asc
+    m = int(order[:min(3, len(nz))].sum()) // min(3, len(nz))
+    L, R = int(nz[0]), int(nz[-1])
+    if R - L + 1 <= s:
+        return L, R - L + 1, m
+    best = None
+    for a in range(L, R - s + 2):
+        b = a + s - 1
+        if a <= m <= b:
+            key = (max(b - m, m - a), a)
+            if best is None or key < best[0]:
+                best = (key, a)
+    return best[1], s, m
+
+
+def test_sampling_against_its_definition(oracle_lib):
+    rng = np.random.default_rng(19)
+    for trial in range(400):
+        nb = int(rng.integers(12, 80))
+        h = np.zeros(nb, np.uint32)
+        kind = trial % 4
+        if kind == 0:      # a binned right-skewed (Gumbel) distribution, as the score histograms
+            x = rng.gumbel(rng.uniform(5, nb - 5), rng.uniform(0.5, 6), size=int(rng.integers(1, 5000)))
+            np.add.at(h, np.clip(x.astype(int), 0, nb - 1), 1)
+        elif kind == 1:    # sparse bins with many equal counts (tie rules)
+            h[rng.choice(nb, size=int(rng.integers(1, nb + 1)), replace=True)] = rng.integers(1, 4)
+        elif kind == 2:    # long flat tails
+            h[:] = rng.integers(0, 3, size=nb)
+        else:              # one or two bins
+            h[rng.integers(nb)] = int(rng.integers(1, 100))
+            if rng.random() < 0.5:
+                h[rng.integers(nb)] = int(rng.integers(1, 100))
+        s = int(rng.integers(1, 40))
+        want = _window_by_definition(h, s)
+        got = oracle_lib.hist_sample(h, s)
+        if want is None:
+            assert got[1] == 0
+        else:
+            assert got == want, (trial, s, h.tolist())
+
+
+def test_sampling_is_exact_within_s_bins(oracle_lib):
+    """At most s non-zero bins from end to end: the sampled distribution is
+    the distribution; and the score histograms of a real search (0.5 log10
+    units a bin) never span 120 bins, so s = 120 keeps every count."""
+    w = configs.OPEN_MEDIUM.with_proteins(120).with_spectra(40)
+    w = dataclasses.replace(w, params=dataclasses.replace(w.params, min_shared=2))
+    prot, spec = synth.make_workload_inputs(w)
+    db = oracle_lib.OracleDb(prot.seq, prot.off, w.mods, w.params)
+    res = db.search(spec)
+    assert res.n_scored.max() > 500
+    for h in res.hist:
+        np.testing.assert_array_equal(oracle_lib.sampled(h, 120), h)
+        nz = np.flatnonzero(h)
+        if len(nz):
+            np.testing.assert_array_equal(oracle_lib.sampled(h, int(nz[-1] - nz[0] + 1)), h)
