@@ -568,6 +568,23 @@ def run_shards(args):
         same = bool(np.array_equal(merged.psm, ref.psm) and np.array_equal(merged.hist, ref.hist)
                     and np.array_equal(merged.n_scored, ref.n_scored))
         identical &= same
+        if name == "lbe":
+            # the partial distributions exchanged sampled (Sampling section):
+            # e-value drift against the exact merge, rows and keys unchanged
+            real = ref.psm["pid"] != 0xFFFFFFFF
+            sampling = {}
+            for sv in (120, 16, 8):
+                sm = shard.local_sharded_search(parts, db, sample=sv).to_host(n, k)
+                rel = np.abs(sm.psm["evalue"][real] / ref.psm["evalue"][real] - 1.0)
+                sampling[str(sv)] = {
+                    "rows_and_keys_identical": bool(np.array_equal(sm.psm["pid"], ref.psm["pid"])
+                                                    and np.array_equal(sm.psm["key"], ref.psm["key"])),
+                    "evalue_rel_drift_max": float(rel.max()) if rel.size else 0.0,
+                    "evalue_rel_drift_median": float(np.median(rel)) if rel.size else 0.0,
+                    "rows_with_changed_evalue": float(np.mean(rel > 0)) if rel.size else 0.0,
+                    "spectra_with_dropped_bins": float(np.mean(np.any(sm.hist != ref.hist, axis=1))),
+                    "bytes_per_spectrum_per_part": 4 * (sv + 1)}
+            sampling["exact_histogram_bytes_per_spectrum_per_part"] = 4 * 256
         wv, mv = np.array(work), np.array(ms)
         res[name] = {"work_cv": float(wv.std() / wv.mean()), "time_cv": float(mv.std() / mv.mean()),
                      "time_max_over_mean": float(mv.max() / mv.mean()), "search_ms_per_part": [round(x, 3) for x in ms],
@@ -585,6 +602,7 @@ def run_shards(args):
         "config": {"workload": workload_desc(w), "spectra": n, "parts": P, "n_peptides": int(n_pep),
                    "lbe_partition_s": t_lbe},
         "partitions": res,
+        "sampled_exchange": sampling,
         "identical_results": identical,
     }
     print(json.dumps(line), flush=True)

@@ -308,6 +308,40 @@ hicops_status hicops_merge_shards(uint32_t n_shards, uint32_t n, uint32_t top_k,
                                   uint32_t evalue_mode, int on_device, void* cuda_stream, hicops_psm* out_psm,
                                   uint32_t* out_hist, uint32_t* out_nscored);
 
+/* ---- sampled partial score distributions (Sampling section and its
+ * figure: a process's partial distribution of one spectrum is reduced to at
+ * most s samples around its mean before it leaves the process; the tails,
+ * which the fit recovers, are pruned first).  A sample is one histogram bin.
+ * The mean is the integer average (rounded down) of the locations of the
+ * three most intense bins (count descending, lower location first; fewer
+ * when fewer bins are non-zero); of the non-zero bins' span, the end farther
+ * from the mean is dropped (the upper end on a tie) while more than s bins
+ * remain.  A record is s + 1 words: word 0 = lo | len << 16, words 1..len the
+ * counts of bins lo .. lo+len-1 (exact), the rest 0; len = 0 for an empty
+ * histogram.  Score histograms of 0.5 log10 units a bin span far fewer than
+ * the paper's s = 120 bins, so at that s the record holds the whole
+ * histogram. */
+#define HICOPS_SAMPLE_S 120u
+
+/* Samples n histograms hist [n * 256] into records out_rec [n * (s + 1)],
+ * 1 <= s <= 256.  on_device = 1: device buffers, enqueued on cuda_stream;
+ * 0: host buffers, the call copies and waits.  Errors: HICOPS_EINVAL (s out
+ * of range, NULL), HICOPS_ECUDA, HICOPS_ENOMEM. */
+hicops_status hicops_hist_sample(uint32_t n, const uint32_t* hist, uint32_t s, uint32_t* out_rec, int on_device,
+                                 void* cuda_stream);
+
+/* Assembles sampled partial distributions (Superstep 4's addition of the
+ * partial distributions): out_hist [n * 256] = per spectrum the sum over the
+ * n_parts parts of their records' counts, rec [n_parts * n * (s + 1)] (part
+ * p's record of spectrum q at (p * n + q) * (s + 1)).  The result goes to
+ * hicops_merge_shards with hist_parts = 1.  Buffers as hicops_hist_sample,
+ * but the call always waits for cuda_stream (it reads back whether every
+ * record was well formed).  Errors as hicops_hist_sample; also HICOPS_EINVAL
+ * for n_parts outside [1, HICOPS_MAX_SHARDS] or a record whose bins leave
+ * [0, 256) or exceed s (out_hist then holds the sums of the valid records). */
+hicops_status hicops_hist_unsample(uint32_t n_parts, uint32_t n, uint32_t s, const uint32_t* rec, uint32_t* out_hist,
+                                   int on_device, void* cuda_stream);
+
 /* ---- host ingest pipeline (Superstep 3's R/I/K sub-tasks: Buffering and
  * Task Scheduling sections, Supplementary Algorithm 2).  MS2 text files
  * ("S <scan> <scan> <precursor m/z>", "Z <charge> <[M+H]+>" (the first Z

@@ -806,3 +806,171 @@ extern "C" hicops_status hicops_merge_shards(uint32_t n_shards, uint32_t n, uint
     if (!on_device) HC_CUDA(cudaStreamSynchronize(s));
     return HICOPS_OK;
 }
+
+// ---- sampled partial score distributions (paper: Sampling section and its
+// figure).  One warp per spectrum; lane l holds bins 8 l .. 8 l + 7.
+namespace hicops {
+namespace {
+
+constexpr uint32_t kBinsPerLane = kHistBins / 32;
+
+// warp-wide best of (count, bin) pairs: higher count, then lower bin
+__device__ __forceinline__ void warp_best(uint32_t& c, uint32_t& j) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint32_t oc = __shfl_xor_sync(0xffffffffu, c, o), oj = __shfl_xor_sync(0xffffffffu, j, o);
+        if (oc > c || (oc == c && oj < j)) { c = oc; j = oj; }
+    }
+}
+
+__global__ void hist_sample_kernel(const uint32_t* __restrict__ hist, uint32_t n, uint32_t s,
+                                   uint32_t* __restrict__ rec) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (q >= n) return;
+    const uint32_t* h = hist + (uint64_t)q * kHistBins;
+    uint32_t v[kBinsPerLane];
+#pragma unroll
+    for (uint32_t i = 0; i < kBinsPerLane; ++i) v[i] = h[lane * kBinsPerLane + i];
+    // support [L, R] of the non-zero bins
+    uint32_t L = kHistBins, R = 0;
+#pragma unroll
+    for (uint32_t i = 0; i < kBinsPerLane; ++i)
+        if (v[i]) { L = min(L, lane * kBinsPerLane + i); R = max(R, lane * kBinsPerLane + i); }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        L = min(L, __shfl_xor_sync(0xffffffffu, L, o));
+        R = max(R, __shfl_xor_sync(0xffffffffu, R, o));
+    }
+    uint32_t* out = rec + (uint64_t)q * (s + 1);
+    uint32_t lo = 0, len = 0;
+    if (L <= R) {
+        // the three most intense bins: three rounds of a warp arg-max, each
+        // winner taken out of the next round
+        uint32_t taken = 0, sum = 0, k = 0;
+        for (int r = 0; r < 3; ++r) {
+            uint32_t c = 0, j = 0xffffffffu;
+#pragma unroll
+            for (uint32_t i = 0; i < kBinsPerLane; ++i) {
+                const uint32_t b = lane * kBinsPerLane + i;
+                if (!((taken >> i) & 1u) && (v[i] > c || (v[i] == c && v[i] && b < j))) { c = v[i]; j = b; }
+            }
+            warp_best(c, j);
+            if (c == 0) break;
+            sum += j;
+            ++k;
+            if (j / kBinsPerLane == lane) taken |= 1u << (j % kBinsPerLane);
+        }
+        const uint32_t m = sum / k;
+        if (R - L + 1 <= s) {
+            lo = L;
+            len = R - L + 1;
+        } else {
+            // pruning the farther end first ends with s bins, the lower side
+            // longer by at most one, unless an end of the support stops it
+            const int dl = (int)(s / 2), dh = (int)((s - 1) / 2);
+            int a = (int)m - dl, b = (int)m + dh;
+            if (a < (int)L) { a = (int)L; b = (int)L + (int)s - 1; }
+            else if (b > (int)R) { b = (int)R; a = (int)R - (int)s + 1; }
+            lo = (uint32_t)a;
+            len = s;
+        }
+    }
+    if (lane == 0) out[0] = lo | (len << 16);
+    for (uint32_t i = lane; i < s; i += 32) out[1 + i] = i < len ? h[lo + i] : 0u;
+}
+
+__global__ void hist_unsample_kernel(const uint32_t* __restrict__ rec, uint32_t n_parts, uint32_t n, uint32_t s,
+                                     uint32_t* __restrict__ hist, uint32_t* __restrict__ bad) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (q >= n) return;
+    uint32_t acc[kBinsPerLane];
+#pragma unroll
+    for (uint32_t i = 0; i < kBinsPerLane; ++i) acc[i] = 0;
+    for (uint32_t p = 0; p < n_parts; ++p) {
+        const uint32_t* r = rec + ((uint64_t)p * n + q) * (s + 1);
+        const uint32_t w0 = r[0], lo = w0 & 0xffffu, len = w0 >> 16;
+        if (len > s || lo + len > kHistBins) {   // not a record of this s
+            if (lane == 0) atomicOr(bad, 1u);
+            continue;
+        }
+#pragma unroll
+        for (uint32_t i = 0; i < kBinsPerLane; ++i) {
+            const uint32_t b = lane * kBinsPerLane + i;
+            if (b >= lo && b < lo + len) acc[i] += r[1 + (b - lo)];
+        }
+    }
+#pragma unroll
+    for (uint32_t i = 0; i < kBinsPerLane; ++i) hist[(uint64_t)q * kHistBins + lane * kBinsPerLane + i] = acc[i];
+}
+
+constexpr int kSampleWarps = 8;
+
+}  // namespace
+}  // namespace hicops
+
+extern "C" hicops_status hicops_hist_sample(uint32_t n, const uint32_t* hist, uint32_t s, uint32_t* out_rec,
+                                            int on_device, void* cuda_stream) {
+    if (s < 1 || s > kHistBins) { set_error("s must be in [1, %u]", kHistBins); return HICOPS_EINVAL; }
+    if (n == 0) return HICOPS_OK;
+    if (!hist || !out_rec) { set_error("NULL argument"); return HICOPS_EINVAL; }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    {
+        Scratch sc(st);
+        const uint32_t* d_h = hist;
+        uint32_t* d_r = out_rec;
+        if (!on_device) {
+            uint32_t* h;
+            HC_CUDA(sc.get(&h, (uint64_t)n * kHistBins));
+            HC_CUDA(sc.get(&d_r, (uint64_t)n * (s + 1)));
+            HC_CUDA(cudaMemcpyAsync(h, hist, sizeof(uint32_t) * n * kHistBins, cudaMemcpyHostToDevice, st));
+            d_h = h;
+        }
+        hist_sample_kernel<<<(n + kSampleWarps - 1) / kSampleWarps, kSampleWarps * 32, 0, st>>>(d_h, n, s, d_r);
+        count_launches(1);
+        HC_CUDA(cudaGetLastError());
+        if (!on_device)
+            HC_CUDA(cudaMemcpyAsync(out_rec, d_r, sizeof(uint32_t) * n * (s + 1), cudaMemcpyDeviceToHost, st));
+    }
+    if (!on_device) HC_CUDA(cudaStreamSynchronize(st));
+    return HICOPS_OK;
+}
+
+extern "C" hicops_status hicops_hist_unsample(uint32_t n_parts, uint32_t n, uint32_t s, const uint32_t* rec,
+                                              uint32_t* out_hist, int on_device, void* cuda_stream) {
+    if (s < 1 || s > kHistBins) { set_error("s must be in [1, %u]", kHistBins); return HICOPS_EINVAL; }
+    if (n_parts < 1 || n_parts > HICOPS_MAX_SHARDS) {
+        set_error("n_parts must be in [1, %u]", (unsigned)HICOPS_MAX_SHARDS);
+        return HICOPS_EINVAL;
+    }
+    if (n == 0) return HICOPS_OK;
+    if (!rec || !out_hist) { set_error("NULL argument"); return HICOPS_EINVAL; }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    uint32_t bad = 0;
+    {
+        Scratch sc(st);
+        const uint32_t* d_r = rec;
+        uint32_t* d_h = out_hist;
+        uint32_t* d_bad;
+        HC_CUDA(sc.get(&d_bad, 1));
+        HC_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(uint32_t), st));
+        if (!on_device) {
+            uint32_t* r;
+            HC_CUDA(sc.get(&r, (uint64_t)n_parts * n * (s + 1)));
+            HC_CUDA(sc.get(&d_h, (uint64_t)n * kHistBins));
+            HC_CUDA(cudaMemcpyAsync(r, rec, sizeof(uint32_t) * n_parts * n * (s + 1), cudaMemcpyHostToDevice, st));
+            d_r = r;
+        }
+        hist_unsample_kernel<<<(n + kSampleWarps - 1) / kSampleWarps, kSampleWarps * 32, 0, st>>>(d_r, n_parts, n, s,
+                                                                                                 d_h, d_bad);
+        count_launches(1);
+        HC_CUDA(cudaGetLastError());
+        if (!on_device)
+            HC_CUDA(cudaMemcpyAsync(out_hist, d_h, sizeof(uint32_t) * n * kHistBins, cudaMemcpyDeviceToHost, st));
+        HC_CUDA(cudaMemcpyAsync(&bad, d_bad, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        HC_CUDA(cudaStreamSynchronize(st));
+    }
+    if (bad) { set_error("a sampled record's bins leave [0, 256) or exceed s"); return HICOPS_EINVAL; }
+    return HICOPS_OK;
+}

@@ -152,6 +152,8 @@ def load(build_if_missing: bool = False):
         "hicops_index_load": (st, [C.c_char_p, C.POINTER(P)]),
         "hicops_merge_shards": (st, [C.c_uint32, C.c_uint32, C.c_uint32, P, P, P, C.c_uint32, C.c_uint32, C.c_int,
                                      P, P, P, P]),
+        "hicops_hist_sample": (st, [C.c_uint32, P, C.c_uint32, P, C.c_int, P]),
+        "hicops_hist_unsample": (st, [C.c_uint32, C.c_uint32, C.c_uint32, P, P, C.c_int, P]),
         "hicops_peptide": (st, [P, C.c_uint32, C.c_char_p, C.c_uint32, P, P]),
         "hicops_index_copy_csr": (st, [P, P, P]),
         "hicops_index_free": (None, [P]),
@@ -542,6 +544,48 @@ def merge_shards_host(n_shards: int, n: int, top_k: int, psm: np.ndarray, hist: 
                        np.zeros(n, np.uint32))
     _check(load().hicops_merge_shards(n_shards, n, top_k, _ptr(psm), _ptr(hist), _ptr(n_scored), hist_parts,
                                       evalue_mode, 0, None, _ptr(out.psm), _ptr(out.hist), _ptr(out.n_scored)))
+    return out
+
+
+# ---- sampled partial score distributions (Sampling section)
+
+SAMPLE_S = 120   # HICOPS_SAMPLE_S, the paper's default number of samples
+
+
+def _is_device(a) -> bool:
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+def hist_sample(hist, s: int = SAMPLE_S, stream=None):
+    """hicops_hist_sample: records [n, s + 1] (word 0 = lo | len << 16, then
+    the kept bins' counts) of histograms [n, 256] or [n * 256].  A device
+    tensor gives a device tensor (asynchronous on the stream), a numpy
+    array a numpy array."""
+    if _is_device(hist):
+        import torch
+        n = hist.numel() // HIST_BINS
+        out = torch.empty(n * (s + 1), dtype=torch.int32, device=hist.device)
+        st = stream if stream is not None else torch.cuda.current_stream()
+        _check(load().hicops_hist_sample(n, hist.data_ptr(), s, out.data_ptr(), 1, st.cuda_stream))
+        return out
+    h = np.ascontiguousarray(hist, np.uint32).reshape(-1, HIST_BINS)
+    out = np.zeros((h.shape[0], s + 1), np.uint32)
+    _check(load().hicops_hist_sample(h.shape[0], _ptr(h), s, _ptr(out), 0, None))
+    return out
+
+
+def hist_unsample(n_parts: int, n: int, rec, s: int = SAMPLE_S, stream=None):
+    """hicops_hist_unsample: the summed histograms [n, 256] of n_parts
+    parts' records [n_parts * n, s + 1]."""
+    if _is_device(rec):
+        import torch
+        out = torch.empty(n * HIST_BINS, dtype=torch.int32, device=rec.device)
+        st = stream if stream is not None else torch.cuda.current_stream()
+        _check(load().hicops_hist_unsample(n_parts, n, s, rec.data_ptr(), out.data_ptr(), 1, st.cuda_stream))
+        return out
+    r = np.ascontiguousarray(rec, np.uint32).reshape(-1, s + 1)
+    out = np.zeros((n, HIST_BINS), np.uint32)
+    _check(load().hicops_hist_unsample(n_parts, n, s, _ptr(r), _ptr(out), 0, None))
     return out
 
 

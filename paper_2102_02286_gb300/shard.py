@@ -19,6 +19,13 @@ One process per shard.  Every rank searches the whole batch against its shard
 ``sharded_search`` runs the three steps on a device batch.  The result equals
 the unsharded search bit for bit, because keys are exact integers and the
 histograms are exact counts.
+
+With ``sample = s`` the partial distributions leave each rank sampled
+(Sampling section: at most s bins around the mean, tails pruned first;
+``hicops.hist_sample``): the ranks all-gather the s + 1-word records instead
+of all-reducing the 256-bin histograms, and ``hicops.hist_unsample`` adds
+them up before the merge.  Top-k rows and candidate counts stay exact; the
+e-value is fitted to the sum of the sampled distributions.
 """
 from __future__ import annotations
 
@@ -70,18 +77,39 @@ def exchange(psm_bytes, hist, n_scored, group=None):
     return torch.cat(parts), hist, n_scored
 
 
+def exchange_sampled(psm_bytes, rec, n_scored, group=None):
+    """Collectives of the sampled merge: returns (rows of every shard; the
+    sampled records of every shard, shard-major; summed candidate counts).
+    n_scored is reduced in place."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    parts = [torch.empty_like(psm_bytes) for _ in range(world)]
+    dist.all_gather(parts, psm_bytes, group=group)
+    recs = [torch.empty_like(rec) for _ in range(world)]
+    dist.all_gather(recs, rec, group=group)
+    dist.all_reduce(n_scored, op=dist.ReduceOp.SUM, group=group)
+    return torch.cat(parts), torch.cat(recs), n_scored
+
+
 def sharded_search(shard_index: hc.Index, dev_batch: hc.DeviceBatch, store, step: int,
-                   timeout_s: float = 30.0, group=None, stream=None) -> hc.DeviceResult:
-    """This rank's shard search of the batch, the exchange and the merge."""
+                   timeout_s: float = 30.0, group=None, stream=None, sample: int = 0) -> hc.DeviceResult:
+    """This rank's shard search of the batch, the exchange and the merge
+    (sample = s > 0: partial distributions exchanged sampled)."""
     import torch.distributed as dist
     rank, world = dist.get_rank(group), dist.get_world_size(group)
     n, k = dev_batch.n, shard_index.top_k
     part = hc.DeviceResult.alloc(n, k)
     shard_index.search_device(dev_batch, part, stream)
+    rec = hc.hist_sample(part.hist, sample, stream) if sample else None
     import torch
     torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
     publish_and_wait(store, step, rank, world, timeout_s)
-    rows, hist, ns = exchange(part.psm, part.hist, part.n_scored, group)
+    if sample:
+        rows, recs, ns = exchange_sampled(part.psm, rec, part.n_scored, group)
+        hist = hc.hist_unsample(world, n, recs, sample, stream)
+    else:
+        rows, hist, ns = exchange(part.psm, part.hist, part.n_scored, group)
     return hc.merge_shards(world, n, k, rows, hist, ns, 1, stream, shard_index.params.evalue_mode)
 
 
@@ -93,9 +121,10 @@ def lbe_parts(index: hc.Index, n_parts: int, upload: bool = True) -> List[hc.Ind
 
 
 def local_sharded_search(shards: List[hc.Index], dev_batch: hc.DeviceBatch,
-                         stream=None) -> hc.DeviceResult:
+                         stream=None, sample: int = 0) -> hc.DeviceResult:
     """All shards on this GPU, one after the other, merged by the device
-    kernel from the per-shard histograms (hist_parts = n_shards)."""
+    kernel from the per-shard histograms (hist_parts = n_shards), or with
+    sample = s > 0 from their sampled records, added up first."""
     import torch
     n, k = dev_batch.n, shards[0].top_k
     P = len(shards)
@@ -103,6 +132,11 @@ def local_sharded_search(shards: List[hc.Index], dev_batch: hc.DeviceBatch,
     for s, out in zip(shards, parts):
         s.search_device(dev_batch, out, stream)
     rows = torch.cat([p.psm for p in parts])
-    hist = torch.cat([p.hist for p in parts])
     ns = torch.cat([p.n_scored for p in parts])
+    if sample:
+        recs = torch.cat([hc.hist_sample(p.hist, sample, stream) for p in parts])
+        hist = hc.hist_unsample(P, n, recs, sample, stream)
+        ns = ns.view(P, n).sum(0, dtype=torch.int32)
+        return hc.merge_shards(P, n, k, rows, hist, ns, 1, stream, shards[0].params.evalue_mode)
+    hist = torch.cat([p.hist for p in parts])
     return hc.merge_shards(P, n, k, rows, hist, ns, P, stream, shards[0].params.evalue_mode)
