@@ -122,10 +122,10 @@ typedef struct hicops_proteins {
  * the index's device, and the call is asynchronous on cuda_stream (results
  * are ready when the stream reaches that point).  on_device = 0: host
  * pointers; the call copies inputs in and results out and returns after the
- * results are in the caller's buffers.  Invalid spectra (charge 0,
- * non-finite precursor, negative tolerance, no peak inside
- * [frag_mz_min, frag_mz_max), more than HICOPS_MAX_PEAKS raw peaks) do not
- * fail the batch: their rows are padding and their histogram is empty. */
+ * results are in the caller's buffers.  A spectrum may hold any number of
+ * raw peaks.  Invalid spectra (charge 0, non-finite precursor, negative
+ * tolerance, no peak inside [frag_mz_min, frag_mz_max)) do not fail the
+ * batch: their rows are padding and their histogram is empty. */
 typedef struct hicops_batch {
     uint32_t n;
     uint32_t on_device;
@@ -137,8 +137,6 @@ typedef struct hicops_batch {
     const double* prec_tol_da; /* [n] precursor mass tolerance dM (Da) */
     void* cuda_stream;         /* cudaStream_t; NULL = legacy default stream */
 } hicops_batch;
-
-#define HICOPS_MAX_PEAKS 4096
 
 /* One peptide-spectrum match.  Padding rows (fewer than top_k candidates or
  * an invalid spectrum): pid = UINT32_MAX, key = INT64_MIN, nb = ny = 0,
@@ -188,7 +186,7 @@ hicops_status hicops_build_index(const hicops_proteins* proteins, const hicops_m
  * superstep-4 e-value).  Outputs: out_psm [n * top_k] rows, spectrum q at
  * rows q*top_k .. q*top_k+top_k-1 in rank order; out_hist [n * 256] or NULL;
  * out_nscored [n] (number of candidates, = sum of the histogram) or NULL.
- * Errors: HICOPS_EINVAL (bad batch, spectrum over HICOPS_MAX_PEAKS peaks,
+ * Errors: HICOPS_EINVAL (bad batch,
  * index not uploaded), HICOPS_ECUDA, HICOPS_ENOMEM. */
 hicops_status hicops_search(hicops_index* index, const hicops_batch* batch, hicops_psm* out_psm,
                             uint32_t* out_hist, uint32_t* out_nscored);
@@ -222,16 +220,24 @@ hicops_status hicops_search(hicops_index* index, const hicops_batch* batch, hico
 hicops_status hicops_search_noalloc(hicops_index* index, const hicops_batch* batch, hicops_psm* out_psm,
                                     uint32_t* out_hist, uint32_t* out_nscored);
 
-/* Measurement helper: per spectrum, the precursor window [lo, hi), the
- * number of retained peaks and the number of index entries inside the window
- * over the retained peaks' buckets (H(q), the work of filter_2).  Any output
- * may be NULL.  Same pointer rules as hicops_search. */
+/* Measurement helper: per spectrum, the precursor window [lo, hi) (Eq. 4's
+ * filter_1), the number of retained peaks and the number of index entries
+ * inside the window over the retained peaks' buckets (H(q), the work of
+ * filter_2, Eq. 4 terms k32'/k33).  Any output may be NULL.  Same pointer
+ * rules and errors as hicops_search. */
 hicops_status hicops_search_work(hicops_index* index, const hicops_batch* batch, uint32_t* out_lo,
                                  uint32_t* out_hi, uint32_t* out_npeaks, uint64_t* out_hits);
 
+/* Sizes of the index: P and the unmodified sequences (Notation section: the
+ * database of D = zeta * 2^m entries), the fragment-index entries and bins
+ * (Superstep 1 items 2-3), device bytes and build times.  The survey's name
+ * hicops_index_stats is the struct's; the call carries get_ so the two do
+ * not collide in C.  Errors: HICOPS_EINVAL (NULL). */
 hicops_status hicops_index_get_stats(const hicops_index* index, hicops_index_stats* out);
 
-/* The parameters the index was built with. */
+/* The parameters the index was built with (the Experimental Setup's
+ * digestion and tolerance settings as this library reads them).  No passage
+ * defines the call itself: a library utility.  Errors: HICOPS_EINVAL (NULL). */
 hicops_status hicops_index_get_params(const hicops_index* index, hicops_params* out);
 
 /* Checkpoint of an index's host half (the digested database: peptide table,
@@ -411,12 +417,20 @@ int hicops_sched_r_to_i(uint32_t qf_len, uint32_t qf_cap, uint32_t n_r);
 
 /* Peptide pid: sequence (NUL-terminated, truncated to cap-1 letters), neutral
  * mass and the bitmask of positions carrying a variable modification (bit j =
- * residue j, 0-based).  Host only. */
+ * residue j, 0-based): the database entry a PSM names (the results of
+ * Supplementary Table 1 list peptide sequences with their modifications).
+ * On a shard or part, pid is a global pid of that shard or part.  Host only.
+ * seq, mass and modmask may be NULL (cap = 0 leaves seq untouched).  Errors:
+ * HICOPS_EINVAL (NULL index, pid not in the index). */
 hicops_status hicops_peptide(const hicops_index* index, uint32_t pid, char* seq, uint32_t cap,
                              double* mass, uint64_t* modmask);
 
-/* Copies the fragment index to host buffers: off [n_bins + 1] bucket
- * offsets and entries [n_entries] = pid << 1 | isY.  Either may be NULL. */
+/* Copies the fragment index (Superstep 1 items 2-3: the model spectra's ions
+ * binned and indexed) to host buffers: off [n_bins + 1] bucket offsets and
+ * entries [n_entries] = pid << 1 | isY, buckets back to back (the device
+ * copy pads each bucket to a multiple of 4 entries; the pads are left out).
+ * Either may be NULL.  Errors: HICOPS_EINVAL (not uploaded), HICOPS_ECUDA,
+ * HICOPS_ENOMEM (host staging of the padded copy). */
 hicops_status hicops_index_copy_csr(const hicops_index* index, uint64_t* off, uint32_t* entries);
 
 /* Launch shape of the search kernel (the paper's R/I/K balancing of
@@ -506,15 +520,21 @@ hicops_status hicops_server_poll(hicops_server* srv, uint64_t ticket, int timeou
  * has). */
 hicops_status hicops_server_cancel(hicops_server* srv, uint64_t ticket);
 
+/* Counters of the server (requests submitted and completed, launches,
+ * spectra, slots): the buffering section's queues observed.  Errors:
+ * HICOPS_EINVAL (NULL). */
 hicops_status hicops_server_get_stats(hicops_server* srv, hicops_server_stats* out);
 
 /* Waits for launched work, drops queued requests, frees the slots. */
 void hicops_server_destroy(hicops_server* srv);
 
 /* Per-phase device time of the last hicops_search on this index, measured
- * with CUDA events recorded on the call's stream.  Measurement only: with
- * timing enabled, concurrent searches on one index overwrite each other's
- * events.  hicops_index_last_timing waits for the last call's end event. */
+ * with CUDA events recorded on the call's stream (the phases of Eq. 4:
+ * preprocessing and filter_1, filter_2 with scoring, the merge).  No passage
+ * defines the call: a measurement utility.  With timing enabled, concurrent
+ * searches on one index overwrite each other's events.
+ * hicops_index_last_timing waits for the last call's end event.  Errors:
+ * HICOPS_EINVAL (not uploaded, timing not enabled), HICOPS_ECUDA. */
 typedef struct hicops_timing {
     float prep_ms;      /* preprocessing + precursor window */
     float plan_ms;      /* work-unit planning (segments, scan) */
@@ -526,12 +546,17 @@ typedef struct hicops_timing {
 hicops_status hicops_index_set_timing(hicops_index* index, int enable);
 hicops_status hicops_index_last_timing(hicops_index* index, hicops_timing* out);
 
-/* Number of CUDA kernels this library has launched in this process. */
+/* Number of CUDA kernels this library has launched in this process.  No
+ * passage: a library utility (it shows that searches ran on the GPU). */
 uint64_t hicops_kernel_launches(void);
 
+/* Frees an index and its device half.  NULL is a no-op.  No passage: a
+ * library utility. */
 void hicops_index_free(hicops_index* index);
 
-/* Thread-local description of the last failure on this thread. */
+/* Thread-local description of the last failure on this thread (never NULL;
+ * owned by the library, valid until the thread's next failing call).  No
+ * passage: a library utility. */
 const char* hicops_last_error(void);
 
 #ifdef __cplusplus

@@ -78,8 +78,21 @@ __device__ __forceinline__ uint64_t mass_bound(const double* mass, uint64_t n, d
     return a;
 }
 
+// Spectra of more than kPrepWarpPeaks raw peaks, one block each, any number
+// of raw peaks: the raw peaks are taken in chunks of kPrepChunk, and each
+// chunk is merged with the running list of the best top_n bins so far (in
+// raw form again: bin << 32 | intensity bits), sorted by bin, reduced to one
+// representative per bin (its largest intensity), re-keyed by (intensity
+// desc, bin asc), sorted, and cut to top_n.  A bin's value in the list only
+// grows, so a bin left out at some chunk has top_n better bins from then on:
+// the final list is the top_n bins of the whole spectrum by their largest
+// intensity (R8), whatever the chunking.
+constexpr int kPrepSort = 4096;                // keys sorted per chunk
+constexpr int kPrepChunk = kPrepSort - (int)kMaxTopN;   // raw peaks per chunk
+
 __global__ void __launch_bounds__(kPrepThreads) prep_kernel(PrepArgs a) {
-    __shared__ uint64_t keys[HICOPS_MAX_PEAKS];
+    __shared__ uint64_t keys[kPrepSort];
+    __shared__ uint64_t best[kMaxTopN];          // the running list, raw form
     __shared__ int s_nrep;
     const uint32_t q = blockIdx.x;
     const uint64_t p0 = a.peak_off[q], p1 = a.peak_off[q + 1];
@@ -88,45 +101,57 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(PrepArgs a) {
     const double prec = a.prec_mz[q];
     const double tol = a.tol[q];
     const uint32_t z = a.charge[q];
-    bool valid = cnt <= HICOPS_MAX_PEAKS && p1 >= p0 && z > 0 && isfinite(prec) && isfinite(tol) && tol >= 0.0;
+    bool valid = p1 >= p0 && z > 0 && isfinite(prec) && isfinite(tol) && tol >= 0.0;
     int keep = 0;
     if (valid && cnt > 0) {
-        const int npow = next_pow2((int)cnt);
-        // key = bin << 32 | intensity bits (positive finite floats order as integers)
-        for (int i = threadIdx.x; i < npow; i += blockDim.x) {
-            uint64_t k = ~0ull;
-            if (i < (int)cnt) {
-                const float m = a.mz[p0 + i], I = a.inten[p0 + i];
-                const double md = (double)m;
-                if (isfinite(m) && isfinite(I) && I > 0.0f && md >= a.mz_lo && md < a.mz_hi) {
-                    const uint32_t bin = (uint32_t)floor(md / a.w);
-                    k = ((uint64_t)bin << 32) | __float_as_uint(I);
+        for (uint64_t base = 0; base < cnt; base += kPrepChunk) {
+            const int m = (int)min((uint64_t)kPrepChunk, cnt - base);
+            const int total = m + keep;
+            const int npow = next_pow2(total);
+            // key = bin << 32 | intensity bits (positive finite floats order as integers)
+            for (int i = threadIdx.x; i < npow; i += blockDim.x) {
+                uint64_t k = ~0ull;
+                if (i < m) {
+                    const float mz = a.mz[p0 + base + i], I = a.inten[p0 + base + i];
+                    const double md = (double)mz;
+                    if (isfinite(mz) && isfinite(I) && I > 0.0f && md >= a.mz_lo && md < a.mz_hi) {
+                        const uint32_t bin = (uint32_t)floor(md / a.w);
+                        k = ((uint64_t)bin << 32) | __float_as_uint(I);
+                    }
+                } else if (i < total) {
+                    k = best[i - m];
                 }
+                keys[i] = k;
             }
-            keys[i] = k;
+            if (threadIdx.x == 0) s_nrep = 0;
+            __syncthreads();
+            bitonic_sort_u64(keys, npow);
+            // one representative per bin: the last (most intense) of each run
+            uint64_t rep[kPrepSort / kPrepThreads];
+            int nr = 0;
+            for (int i = threadIdx.x; i < npow; i += blockDim.x) {
+                const uint64_t k = keys[i];
+                if (k == ~0ull) continue;
+                const bool last = (i + 1 == npow) || ((keys[i + 1] >> 32) != (k >> 32));
+                // re-key: intensity descending, then bin ascending
+                if (last) rep[nr++] = ((uint64_t)(~(uint32_t)k) << 32) | (k >> 32);
+            }
+            __syncthreads();
+            for (int r = 0; r < nr; ++r) keys[atomicAdd(&s_nrep, 1)] = rep[r];
+            __syncthreads();
+            const int nrep = s_nrep;
+            const int npow2 = next_pow2(nrep > 0 ? nrep : 1);
+            for (int i = nrep + threadIdx.x; i < npow2; i += blockDim.x) keys[i] = ~0ull;
+            __syncthreads();
+            bitonic_sort_u64(keys, npow2);
+            keep = nrep < (int)a.topn ? nrep : (int)a.topn;
+            // the running list back in raw form for the next chunk
+            for (int t = threadIdx.x; t < keep; t += blockDim.x) {
+                const uint64_t k = keys[t];
+                best[t] = ((uint64_t)(uint32_t)k << 32) | (uint32_t)~(uint32_t)(k >> 32);
+            }
+            __syncthreads();
         }
-        if (threadIdx.x == 0) s_nrep = 0;
-        __syncthreads();
-        bitonic_sort_u64(keys, npow);
-        // one representative per bin: the last (most intense) of each run
-        uint64_t rep[HICOPS_MAX_PEAKS / kPrepThreads];
-        int nr = 0;
-        for (int i = threadIdx.x; i < npow; i += blockDim.x) {
-            const uint64_t k = keys[i];
-            if (k == ~0ull) continue;
-            const bool last = (i + 1 == npow) || ((keys[i + 1] >> 32) != (k >> 32));
-            // re-key: intensity descending, then bin ascending
-            if (last) rep[nr++] = ((uint64_t)(~(uint32_t)k) << 32) | (k >> 32);
-        }
-        __syncthreads();
-        for (int r = 0; r < nr; ++r) keys[atomicAdd(&s_nrep, 1)] = rep[r];
-        __syncthreads();
-        const int nrep = s_nrep;
-        const int npow2 = next_pow2(nrep > 0 ? nrep : 1);
-        for (int i = nrep + threadIdx.x; i < npow2; i += blockDim.x) keys[i] = ~0ull;
-        __syncthreads();
-        bitonic_sort_u64(keys, npow2);
-        keep = nrep < (int)a.topn ? nrep : (int)a.topn;
         if (keep > 0) {
             const double Imax = (double)__uint_as_float(~(uint32_t)(keys[0] >> 32));
             for (int t = threadIdx.x; t < keep; t += blockDim.x) {

@@ -20,7 +20,6 @@ from .configs import SearchParams
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EOVERFLOW, EBUSY, ECANCELLED = range(8)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ETIMEOUT", "EOVERFLOW", "EBUSY", "ECANCELLED"]
-MAX_PEAKS = 4096
 HIST_BINS = 256
 
 

@@ -159,27 +159,41 @@ def test_edge_cases(gpu, oracle_lib):
         (list(m0), list(i0)),                                  # NaN precursor
         (list(m0), list(i0)),                                  # negative tolerance
         ([50.0, 2500.0, 99.999], [1.0, 2.0, 3.0]),             # nothing in range
-        (list(rng.uniform(100, 2000, 4096)), list(rng.uniform(1, 100, 4096))),   # exactly the maximum
-        (list(rng.uniform(100, 2000, 4097)), list(rng.uniform(1, 100, 4097))),   # one over: invalid
+        (list(rng.uniform(100, 2000, 4096)), list(rng.uniform(1, 100, 4096))),   # one sort's worth of raw peaks
+        (list(rng.uniform(100, 2000, 4097)), list(rng.uniform(1, 100, 4097))),   # one more
         (list(m0) + [float("nan"), 150.0], list(i0) + [5.0, float("inf")]),      # non-finite peaks
         (list(m0), list(i0)),                                  # whole database in the window
         (list(m0), list(i0)),                                  # zero tolerance
+        # 25,000 raw peaks on the peptide's own m/z values, each repeated in
+        # every chunk with other intensities: a bin keeps its largest anywhere
+        (list(np.tile(m0, 25000 // len(m0) + 1)[:25000]), list(rng.uniform(1, 1000, 25000))),
+        # the peptide's peaks after 9,000 weaker noise peaks: the retained
+        # bins all come from the last chunk
+        (list(rng.uniform(100, 2000, 9000)) + list(m0), list(rng.uniform(0.01, 0.1, 9000)) + list(i0 + 1.0)),
     ]
     p0 = float(base.prec_mz[0])
-    prec = [p0, p0, p0, float("nan"), p0, p0, p0, p0, p0, p0, p0]
-    z = [int(base.charge[0])] * 11
+    prec = [p0, p0, p0, float("nan"), p0, p0, p0, p0, p0, p0, p0, p0, p0]
+    z = [int(base.charge[0])] * 13
     z[2] = 0
-    tol = [10.0, 10.0, 10.0, 10.0, -1.0, 10.0, 500.0, 500.0, 10.0, 1e9, 0.0]
+    tol = [10.0, 10.0, 10.0, 10.0, -1.0, 10.0, 500.0, 500.0, 10.0, 1e9, 0.0, 500.0, 10.0]
     spec = synth.spectra_from_lists(peaks, prec, z, tol)
     got = idx.search(spec)
-    sel = [i for i in range(spec.n) if i != 7]
-    ref = db.search(spec, sel=sel)
-    assert_parity(got, ref, sel=sel, label="edge")
-    # over the per-spectrum peak limit: padding rows, empty histogram
-    assert np.all(got.psm["pid"][7] == PAD) and got.n_scored[7] == 0
+    ref = db.search(spec)
+    assert_parity(got, ref, label="edge")
     for q in (1, 2, 3, 4, 5):
         assert np.all(got.psm["pid"][q] == PAD) and got.n_scored[q] == 0
-    assert got.n_scored[0] >= 1
+    # no raw-peak limit: every such spectrum is searched, with the oracle's
+    # retained peaks (count here; bins and intensities through the parity)
+    _, _, npk, _ = idx.search_work(spec)
+    for q in (0, 6, 7, 11, 12):
+        a, b = int(spec.peak_off[q]), int(spec.peak_off[q + 1])
+        bins, _, _, _ = oracle_lib.preprocess(w.params, spec.mz[a:b], spec.intensity[a:b], float(spec.prec_mz[q]),
+                                              int(spec.charge[q]), float(spec.tol_da[q]))
+        assert npk[q] == len(bins) > 0, q
+    for q in (0, 11, 12):
+        assert got.n_scored[q] >= 1, q
+    # the last spectrum retains the peptide's own peaks, so it finds what the first finds
+    assert got.psm["pid"][12][0] == got.psm["pid"][0][0]
 
 
 def test_empty_batch(gpu):
