@@ -682,10 +682,34 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 384 ? 2 : 1) search_kernel
             __syncthreads();
         };
         // Replay of the log: 4 records per thread in flight, then their
-        // twice-plane words, then the inserts of the candidates' entries.
+        // twice-plane words; a candidate's record goes to its warp's queue
+        // (the warp's compaction-list words, free until the epilogue), and a
+        // full queue is inserted into the table with every lane busy, so the
+        // insert loop never runs for one or two lanes.  The loop is
+        // warp-uniform (i0 - lane is the warp's first index).
         auto replay = [&](uint32_t R, uint32_t wlo, uint32_t whi) {
             constexpr int kU = 4;
-            for (uint32_t i0 = tid; i0 < R; i0 += kU * THREADS) {
+            uint32_t* const queue = lists + (uint32_t)warp * kListStride;
+            uint32_t qn = 0;
+            auto flush = [&]() {
+                __syncwarp();   // the other lanes' appends are visible
+                for (uint32_t j = lane; j < qn; j += 32) {
+                    const uint32_t r = queue[j];
+                    const uint32_t off = (r & 0x7ffffu) >> 1;
+                    const uint32_t v = counter_inc_y(r & 1u, sh.pinc[r >> 19]);
+                    const unsigned long long item = ((unsigned long long)off << 32) | v;
+                    uint32_t sl = slot_of(off);
+                    for (uint32_t probe = 0; probe < kSlots; ++probe) {
+                        const unsigned long long old = atomicCAS(&tab[sl], 0ull, item);
+                        if (old == 0ull) break;
+                        if ((uint32_t)(old >> 32) == off) { atomicAdd(&tab[sl], (unsigned long long)v); break; }
+                        sl = (sl + 1) & (kSlots - 1);
+                    }
+                }
+                __syncwarp();
+                qn = 0;
+            };
+            for (uint32_t i0 = tid; i0 - lane < R; i0 += kU * THREADS) {
                 uint32_t rec[kU], tw[kU];
 #pragma unroll
                 for (int u = 0; u < kU; ++u) {
@@ -699,18 +723,14 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 384 ? 2 : 1) search_kernel
                 for (int u = 0; u < kU; ++u) {
                     const uint32_t off = (rec[u] & 0x7ffffu) >> 1;
                     const uint32_t w = off >> 5;
-                    if (rec[u] == 0xffffffffu || !((tw[u] >> (off & 31)) & 1u) || w < wlo || w >= whi) continue;
-                    const uint32_t v = counter_inc_y(rec[u] & 1u, sh.pinc[rec[u] >> 19]);
-                    const unsigned long long item = ((unsigned long long)off << 32) | v;
-                    uint32_t sl = slot_of(off);
-                    for (uint32_t probe = 0; probe < kSlots; ++probe) {
-                        const unsigned long long old = atomicCAS(&tab[sl], 0ull, item);
-                        if (old == 0ull) break;
-                        if ((uint32_t)(old >> 32) == off) { atomicAdd(&tab[sl], (unsigned long long)v); break; }
-                        sl = (sl + 1) & (kSlots - 1);
-                    }
+                    const bool cand = rec[u] != 0xffffffffu && ((tw[u] >> (off & 31)) & 1u) && w >= wlo && w < whi;
+                    const unsigned msk = __ballot_sync(0xffffffffu, cand);
+                    if (qn + 32 > (uint32_t)kListStride) flush();
+                    if (cand) queue[qn + __popc(msk & lt)] = rec[u];
+                    qn += __popc(msk);
                 }
             }
+            flush();
         };
         // Visits the occupied slots.  Warp w compacts the occupied slot
         // indices of its share [w * spw, (w + 1) * spw) into its list words,
