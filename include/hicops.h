@@ -437,7 +437,7 @@ hicops_status hicops_index_copy_csr(const hicops_index* index, uint64_t* off, ui
  * superstep 3 becomes the choice of how spectra and peptide ranges map onto
  * persistent CTAs).  Zero fields take the default.  threads: CTA size, 256,
  * 384 or 512 (default 384 for top_k <= 16, else 256).  chunk_entries: index entries a CTA aims to accumulate per pass
- * over a range of peptide ids, in units of 1024, 1..6 (default 6); the range
+ * over a range of peptide ids, in units of 1024, 1..16 (default 12); the range
  * is sized from the spectrum's entry density.  ctas_per_sm: resident CTAs per
  * SM (0 = as many as fit).  seg_pids: a spectrum's precursor window is split
  * into work units of at least this many peptide ids (0 = split only when the

@@ -119,18 +119,18 @@ hicops_status check_config(const hicops_search_config& c) {
         set_error("threads must be 256, 384 or 512");
         return HICOPS_EINVAL;
     }
-    if (c.chunk_entries > 6) { set_error("chunk_entries must be in 1..6"); return HICOPS_EINVAL; }
+    if (c.chunk_entries > 16) { set_error("chunk_entries must be in 1..16"); return HICOPS_EINVAL; }
     if (c.ctas_per_sm > 8) { set_error("ctas_per_sm must be <= 8"); return HICOPS_EINVAL; }
     return HICOPS_OK;
 }
 
 // Default shape: 384-thread CTAs (two fit an SM while the top-k lists are
-// at most 16 long), else 256; super-chunks of about 6 k entries (the
-// autotuner's choice on the open-search workloads).
+// at most 16 long), else 256; super-chunks of up to about 12 k entries (the
+// planes and the log's room cap sparse spectra's super-chunks earlier).
 hicops_search_config resolved(const hicops_search_config& c, uint32_t k) {
     hicops_search_config r = c;
     if (!r.threads) r.threads = k <= 16 ? 384 : 256;
-    if (!r.chunk_entries) r.chunk_entries = 6;
+    if (!r.chunk_entries) r.chunk_entries = 12;
     return r;
 }
 
@@ -144,15 +144,16 @@ uint32_t max_segments(const hicops_search_config& c, uint32_t n) {
     return m;
 }
 
-template <int KMAX, int THREADS>
+template <int KMAX, int THREADS, int MAXP>
 hicops_status launch_search_t(const SearchArgs& sa, uint32_t ctas_per_sm, uint64_t max_units, cudaStream_t s) {
     static std::atomic<int> occ{-1};   // CTAs per SM; concurrent first calls compute the same value
-    const size_t smem = sizeof(uint32_t) * kDynWords;   // 68 KB: the kernel's planes, log, slots / counters
+    const size_t smem = sizeof(uint32_t) * Layout<KMAX, THREADS, MAXP>::kDynWords;   // planes, log, slots / counters
     if (occ.load(std::memory_order_acquire) < 0) {
-        HC_CUDA(cudaFuncSetAttribute(search_kernel<KMAX, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
+        HC_CUDA(cudaFuncSetAttribute(search_kernel<KMAX, THREADS, MAXP>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int b = 0;
-        HC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, search_kernel<KMAX, THREADS>, THREADS, smem));
+        HC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, search_kernel<KMAX, THREADS, MAXP>, THREADS,
+                                                              smem));
         occ.store(b < 1 ? 1 : b, std::memory_order_release);
     }
     int per_sm = occ.load(std::memory_order_acquire);
@@ -160,17 +161,25 @@ hicops_status launch_search_t(const SearchArgs& sa, uint32_t ctas_per_sm, uint64
     // no more CTAs than work units can exist
     uint64_t grid = (uint64_t)g_sm_count.load(std::memory_order_relaxed) * per_sm;
     if (max_units < grid) grid = max_units ? max_units : 1;
-    search_kernel<KMAX, THREADS><<<(unsigned)grid, THREADS, smem, s>>>(sa);
+    search_kernel<KMAX, THREADS, MAXP><<<(unsigned)grid, THREADS, smem, s>>>(sa);
     count_launches(1);
     HC_CUDA(cudaGetLastError());
     return HICOPS_OK;
 }
 
+// The kernel for at most 512 query bins a spectrum (no fragment tolerance, or
+// a narrow one) has the smaller static shared memory and the larger planes.
+template <int THREADS, int MAXP>
+hicops_status launch_search_p(const SearchArgs& sa, uint32_t ctas_per_sm, uint64_t max_units, cudaStream_t s) {
+    if (sa.k <= 8) return launch_search_t<8, THREADS, MAXP>(sa, ctas_per_sm, max_units, s);
+    if (sa.k <= 16) return launch_search_t<16, THREADS, MAXP>(sa, ctas_per_sm, max_units, s);
+    return launch_search_t<32, THREADS, MAXP>(sa, ctas_per_sm, max_units, s);
+}
+
 template <int THREADS>
 hicops_status launch_search_k(const SearchArgs& sa, uint32_t ctas_per_sm, uint64_t max_units, cudaStream_t s) {
-    if (sa.k <= 8) return launch_search_t<8, THREADS>(sa, ctas_per_sm, max_units, s);
-    if (sa.k <= 16) return launch_search_t<16, THREADS>(sa, ctas_per_sm, max_units, s);
-    return launch_search_t<32, THREADS>(sa, ctas_per_sm, max_units, s);
+    if (sa.topn <= 512) return launch_search_p<THREADS, 512>(sa, ctas_per_sm, max_units, s);
+    return launch_search_p<THREADS, kMaxTopN>(sa, ctas_per_sm, max_units, s);
 }
 
 hicops_status launch_search(const SearchArgs& sa, const hicops_search_config& c, uint64_t max_units,
@@ -484,7 +493,7 @@ extern "C" hicops_status hicops_autotune(hicops_index* idx, const hicops_batch* 
     if (st != HICOPS_OK) return st;
     if (!b->on_device || b->n == 0) { set_error("autotune needs a non-empty device batch"); return HICOPS_EINVAL; }
     const uint32_t cand_threads[2] = {256, 384};
-    const uint32_t cand_cm[5] = {2, 3, 4, 5, 6};   // chunk_entries
+    const uint32_t cand_cm[4] = {4, 8, 12, 16};   // chunk_entries
     const uint32_t cand_ctas[2] = {0, 1};
     const uint32_t cand_seg[3] = {0, 1u << 18, 1u << 16};
     cudaStream_t s = (cudaStream_t)b->cuda_stream;

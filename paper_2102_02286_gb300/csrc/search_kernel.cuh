@@ -44,20 +44,12 @@
 constexpr int kMaxHot = 6;                 // bitmap slices (b or y bitmap of a hot bucket) per spectrum
 constexpr int kMaxWarps = 16;              // CTAs of up to 512 threads
 constexpr int kTouchCap = 3584;            // touched list of a direct-counter column (more: full scan)
-constexpr uint32_t kMaxCols = 12;          // widest super-chunk (columns of kChunk ids)
 constexpr uint32_t kSlots = 1024;          // candidate counters per round
 constexpr uint32_t kRound = 768;           // candidates per round (+31 at most)
-// 68 KB of dynamic shared memory, in 32-bit words; a super-chunk of m columns
-// (W = 512 m words per plane):
-//   [0, W) seen plane | [W, 2W) twice plane | [2W, 2W + R) log |
-//   [kListWord, kSlotWord) slot compaction lists | [kSlotWord, kDynWords) kSlots 64-bit slots;
-// or [0, 16384) direct counters (over lists and slots, which are zero then)
-constexpr uint32_t kDynWords = kChunk + 1024;
-constexpr uint32_t kSlotWord = kDynWords - 2 * kSlots;
-constexpr uint32_t kListWords = 1152;       // compaction lists: up to 3 groups of 32 slots per warp
-constexpr uint32_t kListWord = kSlotWord - kListWords;
-constexpr uint32_t kMaxRounds = kListWord / kRound + 2;
-static_assert(2 * kMaxCols * kChunk / 32 < kListWord, "planes of the widest super-chunk leave room for a log");
+constexpr uint32_t kListWords = 1152;      // compaction lists: up to 3 groups of 32 slots per warp
+constexpr uint32_t kRoundsCap = 32;        // candidate rounds of a super-chunk at most
+constexpr uint32_t kSmemPerCta = 233472 / 2 - 1024;   // shared memory of one of two CTAs on an SM
+
 
 struct SearchArgs {
     const uint32_t* qbin;
@@ -122,18 +114,19 @@ struct WarpTop {
     }
 };
 
+template <int MAXP>
 struct SearchShared {
-    uint64_t pbase[kMaxTopN];         // bucket start of each ordinary peak
-    uint32_t prow[kMaxTopN];          // its skip-table row
-    uint32_t pinc[kMaxTopN];          // its quantised intensity
-    uint32_t pre[2][kMaxTopN + 1];    // exclusive prefix of the run lengths (parity)
-    uint32_t rs[2][kMaxTopN];         // run starts relative to the bucket (parity)
+    uint32_t pbase[MAXP];             // bucket start of each ordinary peak, in 4-entry groups
+    uint32_t prow[MAXP];              // its skip-table row
+    uint32_t pinc[MAXP];              // its quantised intensity
+    uint32_t pre[2][MAXP + 1];        // exclusive prefix of the run lengths (parity)
+    uint32_t rs[2][MAXP];             // run starts relative to the bucket (parity)
     union {
-        uint16_t touched[kTouchCap];  // counters that became non-zero (direct columns)
-        uint16_t hotc[kMaxTopN];      // (classification) hot peaks: index into qbin
+        uint16_t touched[MAXP <= 512 ? 1 : kTouchCap];   // counters that became non-zero (else dynamic)
+        uint16_t hotc[MAXP];          // (classification) hot peaks: index into qbin
     };
     uint16_t wli[2][kMaxWarps];       // peak holding each warp's first entry (parity)
-    uint16_t wb[kMaxRounds + 1];      // first plane word of each candidate round
+    uint16_t wb[kRoundsCap + 1];      // first plane word of each candidate round
     int ntouched;                     // > kTouchCap means the list overflowed
     int nrounds;
     uint32_t ncand[2];                // candidates counted by pass A (alternating super-chunks)
@@ -147,6 +140,35 @@ struct SearchShared {
     uint64_t unit;
     uint32_t q, np;
     uint32_t seg_lo, seg_hi;
+};
+
+// Dynamic shared memory of the kernel for top-k lists of KMAX, CTAs of
+// THREADS and at most MAXP query bins, in 32-bit words: what two CTAs on an
+// SM leave beside their static part.  A super-chunk of m columns (W = 512 m
+// words per plane):
+//   [0, W) seen plane | [W, 2W) twice plane | [2W, 2W + R) log |
+//   [kListWord, kSlotWord) slot compaction lists | [kSlotWord, kDynWords) kSlots 64-bit slots;
+// or [0, 16384) direct counters (lists and slots are zero then), with the
+// direct columns' touched list right above them for MAXP = 512, where the
+// smaller static part leaves the planes and log about 21 k words (about
+// 15.5 k for MAXP = 1024).
+template <int KMAX, int THREADS, int MAXP>
+struct Layout {
+    static constexpr uint32_t kStatic = sizeof(SearchShared<MAXP>) + (THREADS / 32) * sizeof(WarpTop<KMAX>) + 64;
+    static constexpr uint32_t kDynWords = ((kSmemPerCta - kStatic) / 4) & ~31u;
+    static constexpr uint32_t kSlotWord = kDynWords - 2 * kSlots;
+    static constexpr uint32_t kListWord = kSlotWord - kListWords;
+    static constexpr uint32_t kMaxRounds = kListWord / kRound + 2;
+    // widest super-chunk (columns of kChunk ids): planes within the counters'
+    // 16384 words (below the touched list) and 19-bit record offsets, and
+    // room for a log of 2048 words beside the widest planes
+    static constexpr uint32_t kMaxCols = (kListWord - 2048) / 1024 < 16 ? (kListWord - 2048) / 1024 : 16;
+    static constexpr bool kTouchDyn = MAXP <= 512;
+    static_assert(kMaxRounds <= kRoundsCap, "round starts fit");
+    static_assert(kMaxCols >= 1 && 2 * kMaxCols * kChunk / 32 < kListWord, "planes leave room for a log");
+    static_assert(2 * kMaxCols * kChunk / 32 <= kChunk, "planes never reach the touched list");
+    static_assert(!kTouchDyn || kChunk + kTouchCap / 2 <= kListWord, "the touched list lies below the lists");
+    static_assert(kDynWords >= kChunk, "the direct counters fit");
 };
 
 __device__ __forceinline__ uint32_t counter_inc_y(uint32_t isy, uint32_t iq) {
@@ -168,8 +190,8 @@ __device__ __forceinline__ uint32_t group_len(uint32_t ra, uint32_t rb) {
 // Exclusive scan of the ordinary peaks' run lengths (in whole groups), in two
 // halves around a barrier the caller provides.  Thread tid owns peaks
 // tid*ppt .. +ppt-1.
-template <int PPT>
-__device__ __forceinline__ uint32_t scan_runs_1(SearchShared& sh, int nnorm, int ppt, const uint32_t (&ra)[PPT],
+template <int PPT, class SH>
+__device__ __forceinline__ uint32_t scan_runs_1(SH& sh, int nnorm, int ppt, const uint32_t (&ra)[PPT],
                                                 const uint32_t (&rb)[PPT]) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t sum = 0;
@@ -196,8 +218,8 @@ __device__ __forceinline__ uint32_t warp_share(uint32_t total) {
     return ((total + nwarps - 1) / nwarps + 3) & ~3u;
 }
 
-template <int THREADS, int PPT>
-__device__ __forceinline__ void scan_runs_2(SearchShared& sh, int buf, int nnorm, int ppt, uint32_t excl,
+template <int THREADS, int PPT, class SH>
+__device__ __forceinline__ void scan_runs_2(SH& sh, int buf, int nnorm, int ppt, uint32_t excl,
                                             const uint32_t (&ra)[PPT], const uint32_t (&rb)[PPT]) {
     const int tid = threadIdx.x, warp = tid >> 5;
     constexpr int nwarps = THREADS / 32;
@@ -226,16 +248,20 @@ __device__ __forceinline__ void scan_runs_2(SearchShared& sh, int buf, int nnorm
     if (tid == 0) sh.pre[buf][nnorm] = total;
 }
 
-template <int KMAX, int THREADS>
+template <int KMAX, int THREADS, int MAXP>
 __global__ void __launch_bounds__(THREADS, THREADS <= 384 ? 2 : 1) search_kernel(SearchArgs a) {
+    using L = Layout<KMAX, THREADS, MAXP>;
+    constexpr uint32_t kDynWords = L::kDynWords, kSlotWord = L::kSlotWord, kListWord = L::kListWord;
+    constexpr uint32_t kMaxRounds = L::kMaxRounds, kMaxCols = L::kMaxCols;
     extern __shared__ __align__(16) uint32_t smem32[];   // kDynWords words (layout above)
     uint32_t* const cnt = smem32;
     uint32_t* const seen = smem32;
     uint32_t* const lists = smem32 + kListWord;
     unsigned long long* const tab = reinterpret_cast<unsigned long long*>(smem32 + kSlotWord);
-    __shared__ SearchShared sh;
+    __shared__ SearchShared<MAXP> sh;
+    uint16_t* const touched = L::kTouchDyn ? reinterpret_cast<uint16_t*>(smem32 + kChunk) : sh.touched;
     constexpr int nwarps = THREADS / 32;
-    constexpr int PPT = (kMaxTopN + THREADS - 1) / THREADS;   // ordinary peaks per thread (at most)
+    constexpr int PPT = (MAXP + THREADS - 1) / THREADS;   // ordinary peaks per thread (at most)
     constexpr int kListStride = (32 / nwarps + (32 % nwarps ? 1 : 0)) * 32;   // list words per warp
     static_assert(kListStride * nwarps <= (int)kListWords, "compaction lists fit");
     __shared__ WarpTop<KMAX> wtop[nwarps];
@@ -295,7 +321,7 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 384 ? 2 : 1) search_kernel
             const int32_t row = a.skip_row[bin];
             if (row < 0) continue;   // empty bucket
             const int s = atomicAdd(&sh.nnorm, 1);
-            sh.pbase[s] = a.off[bin];
+            sh.pbase[s] = (uint32_t)(a.off[bin] >> 2);
             sh.prow[s] = (uint32_t)row;
             sh.pinc[s] = a.qiq[(uint64_t)q * a.topn + t];
         }
@@ -316,7 +342,7 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 384 ? 2 : 1) search_kernel
                     ++nh;
                 } else {
                     const int s = sh.nnorm++;
-                    sh.pbase[s] = a.off[bin];
+                    sh.pbase[s] = (uint32_t)(a.off[bin] >> 2);
                     sh.prow[s] = (uint32_t)a.skip_row[bin];
                     sh.pinc[s] = iq;
                 }
@@ -393,7 +419,7 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 384 ? 2 : 1) search_kernel
             if (f0 >= f1) return;
             int li = sh.wli[buf][warp];
             uint32_t nxt = sh.pre[buf][li + 1];
-            uint64_t gb = sh.pbase[li] + sh.rs[buf][li] - sh.pre[buf][li];
+            uint64_t gb = ((uint64_t)sh.pbase[li] << 2) + sh.rs[buf][li] - sh.pre[buf][li];
             for (uint32_t fb = f0 + lane; fb < f1; fb += 32 * kJ) {
                 uint32_t ev[kJ];
                 uint32_t lp[kJ];
@@ -406,7 +432,7 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 384 ? 2 : 1) search_kernel
                         while (f >= nxt) {
                             ++li;
                             nxt = sh.pre[buf][li + 1];
-                            gb = sh.pbase[li] + sh.rs[buf][li] - sh.pre[buf][li];
+                            gb = ((uint64_t)sh.pbase[li] << 2) + sh.rs[buf][li] - sh.pre[buf][li];
                         }
                         lp[j] = (uint32_t)li;
                         ev[j] = __ldg(a.entry + (gb + f));
@@ -466,7 +492,7 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 384 ? 2 : 1) search_kernel
                 }
                 if (first) {
                     const int slot = atomicAdd(&sh.ntouched, 1);
-                    if (slot < kTouchCap) sh.touched[slot] = (uint16_t)off;
+                    if (slot < kTouchCap) touched[slot] = (uint16_t)off;
                 }
             });
             __syncthreads();
@@ -475,7 +501,7 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 384 ? 2 : 1) search_kernel
                 for (int i0 = warp * 32; i0 < nt; i0 += THREADS) {   // warp-uniform trip count
                     const int i = i0 + lane;
                     if (i < nt) {
-                        const uint32_t w = sh.touched[i];
+                        const uint32_t w = touched[i];
                         const uint32_t c = cnt[w];
                         cnt[w] = 0u;
                         visit(c, cb + w);
@@ -546,7 +572,7 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 384 ? 2 : 1) search_kernel
             if (f0 < f1) {
                 int li = sh.wli[buf][warp];
                 uint32_t nxt = sh.pre[buf][li + 1];
-                const uint32_t* gp = a.entry + (sh.pbase[li] + sh.rs[buf][li] - sh.pre[buf][li]);
+                const uint32_t* gp = a.entry + (((uint64_t)sh.pbase[li] << 2) + sh.rs[buf][li] - sh.pre[buf][li]);
                 uint32_t lsh = (uint32_t)li << 19;
                 // entries of pids in [x0, x1): e - e_lo < e_span (unsigned)
                 const uint32_t e_lo = x0 << 1, e_span = (x1 - x0) << 1, e_cb = cb << 1;
@@ -563,7 +589,7 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 384 ? 2 : 1) search_kernel
                             while (f >= nxt) {
                                 ++li;
                                 nxt = sh.pre[buf][li + 1];
-                                gp = a.entry + (sh.pbase[li] + sh.rs[buf][li] - sh.pre[buf][li]);
+                                gp = a.entry + (((uint64_t)sh.pbase[li] << 2) + sh.rs[buf][li] - sh.pre[buf][li]);
                                 lsh = (uint32_t)li << 19;
                             }
                             lr[g] = lsh;

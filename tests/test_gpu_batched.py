@@ -34,7 +34,7 @@ def same(a, b):
 
 
 @pytest.mark.parametrize("threads", [256, 384, 512])
-@pytest.mark.parametrize("chunk_entries", [1, 2, 6])
+@pytest.mark.parametrize("chunk_entries", [1, 2, 6, 16])
 @pytest.mark.parametrize("seg_pids", [0, 1 << 14, 1 << 16])
 def test_launch_shapes_identical(setup, threads, chunk_entries, seg_pids):
     torch, w, prot, idx, spec, ref = setup
@@ -87,7 +87,7 @@ def test_autotune_keeps_results(setup):
     torch, w, prot, idx, spec, ref = setup
     db = hc.DeviceBatch.from_spectra(spec)
     best, ms = idx.autotune(db)
-    assert best.threads in (256, 384, 512) and 1 <= best.chunk_entries <= 6 and ms > 0
+    assert best.threads in (256, 384, 512) and 1 <= best.chunk_entries <= 16 and ms > 0
     try:
         same(idx.search(spec), ref)
     finally:
