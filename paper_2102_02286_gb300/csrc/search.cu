@@ -235,20 +235,25 @@ hicops_status enqueue_search(hicops_index* idx, const DevBatch& d, uint32_t n, c
     count_launches(1);
     HC_CUDA(cudaGetLastError());
     HC_CUDA(exclusive_scan<uint32_t>(w.nseg, n, w.seg_off, w.seg_off + n, w.stmp, s));
-    HC_CUDA(cudaMemsetAsync(w.ocnt, 0, sizeof(uint32_t) * kOrderBuckets, s));
-    order_count_kernel<<<(n + 255) / 256, 256, 0, s>>>(w.qn, w.lo, w.hi, w.seg_off, n, w.ocnt);
-    order_scan_kernel<<<1, 32, 0, s>>>(w.ocnt);
-    order_scatter_kernel<<<(n + 255) / 256, 256, 0, s>>>(w.qn, w.lo, w.hi, w.seg_off, n, w.ocnt + kOrderBuckets,
-                                                         w.order);
-    count_launches(3);
-    HC_CUDA(cudaGetLastError());
+    // longest units first; a small batch has too few units per CTA for the
+    // order to matter, and its three kernels would be most of its launch cost
+    const bool ordered = n >= kOrderMinSpectra;
+    if (ordered) {
+        HC_CUDA(cudaMemsetAsync(w.ocnt, 0, sizeof(uint32_t) * kOrderBuckets, s));
+        order_count_kernel<<<(n + 255) / 256, 256, 0, s>>>(w.qn, w.lo, w.hi, w.seg_off, n, w.ocnt);
+        order_scan_kernel<<<1, 32, 0, s>>>(w.ocnt);
+        order_scatter_kernel<<<(n + 255) / 256, 256, 0, s>>>(w.qn, w.lo, w.hi, w.seg_off, n, w.ocnt + kOrderBuckets,
+                                                             w.order);
+        count_launches(3);
+        HC_CUDA(cudaGetLastError());
+    }
     HC_CUDA(cudaMemsetAsync(d_hist, 0, sizeof(uint32_t) * n * kHistBins, s));
     HC_CUDA(cudaMemsetAsync(d_ns, 0, sizeof(uint32_t) * n, s));
     HC_CUDA(cudaMemsetAsync(w.work, 0, sizeof(unsigned long long), s));
     SearchArgs sa{w.qbin, w.qiq, w.qn, w.lo, w.hi, w.seg_off, n, query_bins_cap(p), di.off, di.entry,
                   di.skip_row, di.skip, di.skip_stride, di.hot_id, di.hot_b, di.hot_y, di.hot_flags,
                   di.hot_words, di.lf, di.ls, (uint32_t)idx->s_max, p.min_shared, k, cfg.chunk_entries * 1024u, w.utop, d_hist, d_ns,
-                  w.work, w.order};
+                  w.work, ordered ? w.order : nullptr};
     mark(idx, 2, s, timing_marks);
     st = launch_search(sa, cfg, (uint64_t)n * max_seg, s);
     if (st != HICOPS_OK) return st;

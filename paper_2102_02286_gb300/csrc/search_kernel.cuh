@@ -80,7 +80,7 @@ struct SearchArgs {
     uint32_t* hist;             // [n * 256]
     uint32_t* nscored;          // [n]
     unsigned long long* work;   // unit counter
-    const uint32_t* order;      // [units] the units in the order they are taken (longest first)
+    const uint32_t* order;      // [units] the units in the order they are taken (longest first), or NULL
 };
 
 __device__ __forceinline__ bool better(int64_t ka, uint32_t pa, int64_t kb, uint32_t pb) {
@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 384 ? 2 : 1) search_kernel
     for (;;) {
         if (tid == 0) {
             const uint64_t t = atomicAdd(a.work, 1ull);
-            const uint64_t u = t < total_units ? (uint64_t)a.order[t] : t;
+            const uint64_t u = t < total_units && a.order ? (uint64_t)a.order[t] : t;
             sh.unit = u;
             sh.nnorm = 0;
             sh.nhotc = 0;

@@ -298,6 +298,7 @@ __global__ void plan_kernel(const uint32_t* __restrict__ qn, const uint32_t* __r
 // buckets, descending), block histograms first so that the global atomics
 // stay few.
 constexpr int kOrderBuckets = 64;
+constexpr uint32_t kOrderMinSpectra = 2048;   // smaller batches take their units in spectrum order
 
 __device__ __forceinline__ int order_bucket(const uint32_t* qn, const uint32_t* lo, const uint32_t* hi,
                                             const uint64_t* seg_off, uint32_t q, uint32_t* ns) {
