@@ -71,6 +71,7 @@ struct Workspace {
     UnitTop* utop = nullptr;
     unsigned long long* work = nullptr;
     uint32_t* order = nullptr;   // [cap_n * max_seg] units, longest first
+    uint32_t* order_q = nullptr; // [cap_n * max_seg] their spectra
     uint32_t* ocnt = nullptr;    // [2 * kOrderBuckets] bucket counts and starts
     hicops_psm* psm = nullptr;   // used when the caller gives no device output
     uint32_t* hist = nullptr;
@@ -93,6 +94,7 @@ hicops_status alloc_workspace(A& al, const hicops_params& p, uint32_t cap_n, uin
     HC_CUDA(al.get(&w.utop, (uint64_t)cap_n * max_seg * p.top_k));
     HC_CUDA(al.get(&w.work, 1));
     HC_CUDA(al.get(&w.order, (uint64_t)cap_n * max_seg));
+    HC_CUDA(al.get(&w.order_q, (uint64_t)cap_n * max_seg));
     HC_CUDA(al.get(&w.ocnt, 2 * kOrderBuckets));
     if (outputs) {
         HC_CUDA(al.get(&w.psm, (uint64_t)cap_n * p.top_k));
@@ -243,7 +245,7 @@ hicops_status enqueue_search(hicops_index* idx, const DevBatch& d, uint32_t n, c
         order_count_kernel<<<(n + 255) / 256, 256, 0, s>>>(w.qn, w.lo, w.hi, w.seg_off, n, w.ocnt);
         order_scan_kernel<<<1, 32, 0, s>>>(w.ocnt);
         order_scatter_kernel<<<(n + 255) / 256, 256, 0, s>>>(w.qn, w.lo, w.hi, w.seg_off, n, w.ocnt + kOrderBuckets,
-                                                             w.order);
+                                                             w.order, w.order_q);
         count_launches(3);
         HC_CUDA(cudaGetLastError());
     }
@@ -253,7 +255,7 @@ hicops_status enqueue_search(hicops_index* idx, const DevBatch& d, uint32_t n, c
     SearchArgs sa{w.qbin, w.qiq, w.qn, w.lo, w.hi, w.seg_off, n, query_bins_cap(p), di.off, di.entry,
                   di.skip_row, di.skip, di.skip_stride, di.hot_id, di.hot_b, di.hot_y, di.hot_flags,
                   di.hot_words, di.lf, di.ls, (uint32_t)idx->s_max, p.min_shared, k, cfg.chunk_entries * 1024u, w.utop, d_hist, d_ns,
-                  w.work, ordered ? w.order : nullptr};
+                  w.work, ordered ? w.order : nullptr, w.order_q};
     mark(idx, 2, s, timing_marks);
     st = launch_search(sa, cfg, (uint64_t)n * max_seg, s);
     if (st != HICOPS_OK) return st;
@@ -599,7 +601,7 @@ constexpr uint64_t noalloc_bytes(uint64_t cap) {
            + 4096                                                // scan temporaries
            + align256(sizeof(UnitTop) * cap * kNoAllocSegs * kMaxTopK)
            + 256                                                 // work counter
-           + align256(4 * cap * kNoAllocSegs)                    // unit order
+           + 2 * align256(4 * cap * kNoAllocSegs)                // unit order and its spectra
            + align256(4 * 2 * kOrderBuckets)                     // its bucket counts
            + align256(sizeof(hicops_psm) * cap * kMaxTopK)       // psm (unused here)
            + align256(4 * cap * kHistBins) + align256(4 * cap);  // hist, n_scored

@@ -81,6 +81,7 @@ struct SearchArgs {
     uint32_t* nscored;          // [n]
     unsigned long long* work;   // unit counter
     const uint32_t* order;      // [units] the units in the order they are taken (longest first), or NULL
+    const uint32_t* order_q;    // [units] the spectrum of each of them
 };
 
 __device__ __forceinline__ bool better(int64_t ka, uint32_t pa, int64_t kb, uint32_t pb) {
@@ -282,7 +283,8 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 384 ? 2 : 1) search_kernel
     for (;;) {
         if (tid == 0) {
             const uint64_t t = atomicAdd(a.work, 1ull);
-            const uint64_t u = t < total_units && a.order ? (uint64_t)a.order[t] : t;
+            const bool listed = t < total_units && a.order;
+            const uint64_t u = listed ? (uint64_t)a.order[t] : t;
             sh.unit = u;
             sh.nnorm = 0;
             sh.nhotc = 0;
@@ -290,12 +292,15 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 384 ? 2 : 1) search_kernel
             sh.nhotpeaks = 0;
             sh.ntouched = 0;
             if (u < total_units) {
-                // spectrum owning unit u: last q with seg_off[q] <= u
+                // spectrum owning unit u (without an order list: the last q
+                // with seg_off[q] <= u)
                 uint32_t lo_q = 0, hi_q = a.n;
-                while (hi_q - lo_q > 1) {
-                    const uint32_t m = (lo_q + hi_q) >> 1;
-                    if (a.seg_off[m] <= u) lo_q = m; else hi_q = m;
-                }
+                if (listed) lo_q = a.order_q[t];
+                else
+                    while (hi_q - lo_q > 1) {
+                        const uint32_t m = (lo_q + hi_q) >> 1;
+                        if (a.seg_off[m] <= u) lo_q = m; else hi_q = m;
+                    }
                 const uint32_t q = lo_q;
                 const uint32_t s = (uint32_t)(u - a.seg_off[q]);
                 const uint32_t ns = (uint32_t)(a.seg_off[q + 1] - a.seg_off[q]);
@@ -326,29 +331,52 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 384 ? 2 : 1) search_kernel
             sh.pinc[s] = a.qiq[(uint64_t)q * a.topn + t];
         }
         __syncthreads();
-        if (tid == 0) {
-            // bitmap slices in peak order while they last; the rest are ordinary
-            int ns = 0, nh = 0;
-            for (int c = 0; c < sh.nhotc; ++c) {
-                const uint32_t t = sh.hotc[c];
-                const uint32_t bin = a.qbin[(uint64_t)q * a.topn + t];
-                const uint32_t iq = a.qiq[(uint64_t)q * a.topn + t];
-                const int32_t hid = a.hot_id[bin];
-                const uint32_t fl = a.hot_flags[hid];
+        if (warp == 0) {
+            // bitmap slices for the hot peaks while they last (warp 0, 32
+            // hot peaks at a time: lanes load their peaks' tables together,
+            // a prefix of slices needed picks the takers); the rest are
+            // streamed like ordinary peaks.  Which hot peaks get slices does
+            // not change any result.
+            int ns = 0, nh = 0;   // warp-uniform
+            const int nhc = sh.nhotc;
+            for (int c0 = 0; c0 < nhc; c0 += 32) {
+                const int c = c0 + lane;
+                const bool act = c < nhc;
+                uint32_t bin = 0, iq = 0, fl = 0;
+                int32_t hid = 0;
+                if (act) {
+                    const uint32_t t = sh.hotc[c];
+                    bin = a.qbin[(uint64_t)q * a.topn + t];
+                    iq = a.qiq[(uint64_t)q * a.topn + t];
+                    hid = a.hot_id[bin];
+                    fl = a.hot_flags[hid];
+                }
                 const int need = (fl & 1u ? 1 : 0) + (fl & 2u ? 1 : 0);
-                if (ns + need <= kMaxHot) {
-                    if (fl & 1u) { sh.slice[ns] = a.hot_b + (uint64_t)hid * a.hot_words; sh.slice_inc[ns++] = (1u << kNbShift) + iq; }
-                    if (fl & 2u) { sh.slice[ns] = a.hot_y + (uint64_t)hid * a.hot_words; sh.slice_inc[ns++] = (1u << kNyShift) + iq; }
-                    ++nh;
-                } else {
-                    const int s = sh.nnorm++;
+                int incl = need;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int x = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += x;
+                }
+                const bool take = act && ns + incl <= kMaxHot;   // a prefix of the lanes
+                if (take) {
+                    int p = ns + incl - need;
+                    if (fl & 1u) { sh.slice[p] = a.hot_b + (uint64_t)hid * a.hot_words; sh.slice_inc[p++] = (1u << kNbShift) + iq; }
+                    if (fl & 2u) { sh.slice[p] = a.hot_y + (uint64_t)hid * a.hot_words; sh.slice_inc[p] = (1u << kNyShift) + iq; }
+                } else if (act) {
+                    const int s = atomicAdd(&sh.nnorm, 1);
                     sh.pbase[s] = (uint32_t)(a.off[bin] >> 2);
                     sh.prow[s] = (uint32_t)a.skip_row[bin];
                     sh.pinc[s] = iq;
                 }
+                const unsigned tm = __ballot_sync(0xffffffffu, take);
+                nh += __popc(tm);
+                if (tm) ns += __shfl_sync(0xffffffffu, incl, 31 - __clz(tm));   // the last taker's prefix
             }
-            sh.nslices = ns;
-            sh.nhotpeaks = nh;
+            if (lane == 0) {
+                sh.nslices = ns;
+                sh.nhotpeaks = nh;
+            }
         }
         __syncthreads();
         const int nnorm = sh.nnorm, nslices = sh.nslices;

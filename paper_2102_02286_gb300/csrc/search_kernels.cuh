@@ -343,7 +343,8 @@ __global__ void order_scan_kernel(uint32_t* __restrict__ cnt) {
 
 __global__ void order_scatter_kernel(const uint32_t* __restrict__ qn, const uint32_t* __restrict__ lo,
                                      const uint32_t* __restrict__ hi, const uint64_t* __restrict__ seg_off,
-                                     uint32_t n, uint32_t* __restrict__ cursor, uint32_t* __restrict__ order) {
+                                     uint32_t n, uint32_t* __restrict__ cursor, uint32_t* __restrict__ order,
+                                     uint32_t* __restrict__ order_q) {
     __shared__ uint32_t bc[kOrderBuckets], bb[kOrderBuckets];
     for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x) bc[i] = 0;
     __syncthreads();
@@ -361,7 +362,10 @@ __global__ void order_scatter_kernel(const uint32_t* __restrict__ qn, const uint
     if (ns) {
         const uint32_t pos = bb[b] + local;
         const uint64_t u0 = seg_off[q];
-        for (uint32_t s = 0; s < ns; ++s) order[pos + s] = (uint32_t)(u0 + s);
+        for (uint32_t s = 0; s < ns; ++s) {
+            order[pos + s] = (uint32_t)(u0 + s);
+            order_q[pos + s] = q;
+        }
     }
 }
 
