@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 384 ? 2 : 1) search_kernel
 #pragma unroll
             for (int w = 0; w < nwarps; ++w) total += sh.wsum[w];
             const uint32_t ncols = col_end - col_lo;
-            if (!hot_alone) {
+            {
                 // about target_entries entries, and planes (1024 words a
                 // column) plus 1.25 times the mean log within kListWord
                 // words, so that denser-than-mean super-chunks still fit
@@ -653,57 +653,85 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 384 ? 2 : 1) search_kernel
         // bits when once_counts), its count and the rounds; clears the seen
         // plane.  Warp w owns words [w * wpw, (w + 1) * wpw), lane l every
         // 32nd of them (barriers inside).
-        auto mark = [&](uint32_t cb, uint32_t words) {
+        auto mark = [&](uint32_t cb, uint32_t words, uint32_t x0, uint32_t x1) {
             const uint32_t G = words >> 5;          // groups of 32 plane words, split evenly over the warps
             const uint32_t g0 = (uint32_t)warp * G / nwarps, g1 = (uint32_t)(warp + 1) * G / nwarps;
             const uint32_t wbeg = g0 << 5, wpw = (g1 - g0) << 5;
             uint32_t mine = 0;
-            // lane l takes the 4 words wbeg + 4 l + 128 j: 16-byte plane
-            // reads, and one 16-byte bitmap read per hot slice, all slices'
-            // reads in flight together
+            // lane l takes the 4 words wbeg + i0 + 4 l (i0 = 0, 128, ...:
+            // warp-uniform trips): 16-byte plane reads, and one 16-byte
+            // bitmap read per hot slice, all slices' reads in flight together
             const uint32_t need = min_shared - 1;   // <= nslices <= kMaxHot when once_counts
-            for (uint32_t i = 4u * lane; i < wpw; i += 128u) {
-                const uint32_t w = wbeg + i;
-                const uint4 s4 = *reinterpret_cast<const uint4*>(seen + w);
-                uint4 c4 = *reinterpret_cast<const uint4*>(twice + w);
-                if (s4.x | s4.y | s4.z | s4.w) {
-                    *reinterpret_cast<uint4*>(seen + w) = make_uint4(0u, 0u, 0u, 0u);
-                    if (once_counts) {
-                        uint4 h[kMaxHot];
+            for (uint32_t i0 = 0; i0 < wpw; i0 += 128u) {
+                const uint32_t w = wbeg + i0 + 4u * lane;
+                const bool act = i0 + 4u * lane < wpw;
+                uint4 s4 = make_uint4(0u, 0u, 0u, 0u), c4 = s4;
+                if (act) {
+                    s4 = *reinterpret_cast<const uint4*>(seen + w);
+                    c4 = *reinterpret_cast<const uint4*>(twice + w);
+                }
+                const bool any_s = (s4.x | s4.y | s4.z | s4.w) != 0u;
+                if (any_s) *reinterpret_cast<uint4*>(seen + w) = make_uint4(0u, 0u, 0u, 0u);
+                uint32_t ho[4] = {0u, 0u, 0u, 0u};   // hot_alone: peptides of no ordinary hit that qualify
+                if (act && once_counts && (any_s || hot_alone)) {
+                    uint4 h[kMaxHot];
 #pragma unroll
-                        for (int sl = 0; sl < kMaxHot; ++sl)
-                            h[sl] = sl < nslices ? __ldg(reinterpret_cast<const uint4*>(sh.slice[sl] + (cb >> 5) + w))
-                                                 : make_uint4(0u, 0u, 0u, 0u);
-                        // per peptide, peptides seen once with at least need
-                        // hot bits (b1, b2: the count's two low bits, b3: 4 or
-                        // more; a superset when need >= 4: visit() is exact)
-                        auto enough = [&](uint32_t s1, uint32_t c2, auto pick) {
-                            uint32_t b1 = 0, b2 = 0, b3 = 0;
+                    for (int sl = 0; sl < kMaxHot; ++sl)
+                        h[sl] = sl < nslices ? __ldg(reinterpret_cast<const uint4*>(sh.slice[sl] + (cb >> 5) + w))
+                                             : make_uint4(0u, 0u, 0u, 0u);
+                    // per peptide its hot-bit count (b1, b2: the two low bits,
+                    // b3: 4 or more): seen once with at least need hot bits
+                    // joins the candidates; seen never with at least
+                    // min_shared is scored here (supersets for need or
+                    // min_shared above 3: visit() is exact)
+                    auto at_least = [](uint32_t b1, uint32_t b2, uint32_t b3, uint32_t t) {
+                        if (t == 0) return 0xffffffffu;
+                        if (t == 1) return b1 | b2 | b3;
+                        if (t == 2) return b2 | b3;
+                        if (t == 3) return (b2 & b1) | b3;
+                        return b3;
+                    };
+                    auto word = [&](uint32_t s1, uint32_t& c2, uint32_t& hot_only, auto pick) {
+                        uint32_t b1 = 0, b2 = 0, b3 = 0;
 #pragma unroll
-                            for (int sl = 0; sl < kMaxHot; ++sl) {
-                                const uint32_t hh = pick(h[sl]);
-                                const uint32_t k1 = b1 & hh;
-                                b1 ^= hh;
-                                const uint32_t k2 = b2 & k1;
-                                b2 ^= k1;
-                                b3 |= k2;
-                            }
-                            uint32_t e;
-                            if (need == 0) e = 0xffffffffu;
-                            else if (need == 1) e = b1 | b2 | b3;
-                            else if (need == 2) e = b2 | b3;
-                            else if (need == 3) e = (b2 & b1) | b3;
-                            else e = b3;
-                            return c2 | (s1 & e);
-                        };
-                        c4.x = enough(s4.x, c4.x, [](const uint4& v) { return v.x; });
-                        c4.y = enough(s4.y, c4.y, [](const uint4& v) { return v.y; });
-                        c4.z = enough(s4.z, c4.z, [](const uint4& v) { return v.z; });
-                        c4.w = enough(s4.w, c4.w, [](const uint4& v) { return v.w; });
-                        *reinterpret_cast<uint4*>(twice + w) = c4;
-                    }
+                        for (int sl = 0; sl < kMaxHot; ++sl) {
+                            const uint32_t hh = pick(h[sl]);
+                            const uint32_t k1 = b1 & hh;
+                            b1 ^= hh;
+                            const uint32_t k2 = b2 & k1;
+                            b2 ^= k1;
+                            b3 |= k2;
+                        }
+                        c2 |= s1 & at_least(b1, b2, b3, need);
+                        if (hot_alone) hot_only = ~s1 & at_least(b1, b2, b3, min_shared);
+                    };
+                    word(s4.x, c4.x, ho[0], [](const uint4& v) { return v.x; });
+                    word(s4.y, c4.y, ho[1], [](const uint4& v) { return v.y; });
+                    word(s4.z, c4.z, ho[2], [](const uint4& v) { return v.z; });
+                    word(s4.w, c4.w, ho[3], [](const uint4& v) { return v.w; });
+                    if (any_s) *reinterpret_cast<uint4*>(twice + w) = c4;
                 }
                 mine += __popc(c4.x) + __popc(c4.y) + __popc(c4.z) + __popc(c4.w);
+                if (hot_alone) {
+                    // score them now (they are in no log), inside [x0, x1)
+#pragma unroll
+                    for (int kw = 0; kw < 4; ++kw) {
+                        const uint32_t gp = cb + ((w + (uint32_t)kw) << 5);
+                        const uint32_t lo_b = x0 > gp ? min(x0 - gp, 32u) : 0u;
+                        const uint32_t hi_b = x1 > gp ? min(x1 - gp, 32u) : 0u;
+                        const uint32_t valid = (hi_b >= 32u ? 0xffffffffu : ((1u << hi_b) - 1u)) &
+                                               ~(lo_b >= 32u ? 0xffffffffu : ((1u << lo_b) - 1u));
+                        uint32_t msk = ho[kw] & valid;
+                        while (__any_sync(0xffffffffu, msk != 0u)) {
+                            if (msk) {
+                                const int b = __ffs(msk) - 1;
+                                msk &= msk - 1;
+                                visit(0u, gp + (uint32_t)b);
+                            }
+                            flush();
+                        }
+                    }
+                }
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
@@ -832,7 +860,7 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 384 ? 2 : 1) search_kernel
         while (c < col_end) {
             const uint32_t R = sh.pre[buf][nnorm];
             const uint32_t words = ((e - c) << kChunkShift) >> 5;
-            const bool direct = hot_alone || 2 * words + R > kListWord;
+            const bool direct = 2 * words + R > kListWord;
             // words [log_lo, log_dirty) may hold old log records: clear them
             // before they become counters or this super-chunk's planes
             if (log_dirty > log_lo && (direct || 2 * words > log_lo)) {
@@ -886,7 +914,7 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 384 ? 2 : 1) search_kernel
             const uint32_t ncand = sh.ncand[par];
             if (tid == 0) sh.ncand[par ^ 1] = 0u;         // the next super-chunk's count
             if (once_counts || ncand > kRound) {
-                mark(cbase, words);                       // two barriers inside
+                mark(cbase, words, x0, x1);               // two barriers inside
                 const int nr = sh.nrounds;
                 for (int r = 0; r < nr; ++r) {
                     const uint32_t wlo = sh.wb[r];
