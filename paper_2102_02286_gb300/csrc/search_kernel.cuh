@@ -10,22 +10,27 @@
 // Almost every peptide in a precursor window is hit by at most one ordinary
 // peak, and with fewer than min_shared - 1 hot slices such a peptide cannot
 // reach min_shared.  So a super-chunk is searched as:
-//   pass A  every index entry (all ordinary peaks' runs laid end to end by a
-//           prefix sum; lane l of a warp takes entries l, l + 32, ...) sets
-//           the peptide's bit in a "seen" bit-plane and, when it was set, in
-//           a "twice" plane (shared-memory atomicOr), and is logged in shared
-//           memory as (peptide offset << 1 | isY | peak << 19); first bits
-//           set in the twice plane are counted;
+//   pass A  every index entry (all ordinary peaks' runs, rounded out to
+//           16-byte groups, laid end to end by a prefix sum; lane l of a warp
+//           takes the 4-entry groups 4 l, 4 l + 128, ..., one 16-byte load
+//           each) sets the peptide's bit in a "seen" bit-plane and, when it
+//           was set, in a "twice" plane (shared-memory atomicOr), and is
+//           logged in shared memory as (peptide offset << 1 | isY | peak <<
+//           19); first bits set in the twice plane are counted;
 //   mark    only when nslices >= min_shared - 1 (peptides seen once with
 //           enough hot bits are candidates too) or when there are more than
-//           kRound candidates: the planes are scanned, candidates counted and
-//           split into rounds of at most kRound candidates by runs of whole
-//           plane words; otherwise there is one round of the twice plane;
-//   replay  per round, the log is walked and every entry of a candidate adds
-//           (1 << 26 | iq) for a b ion or (1 << 20 | iq) for a y ion to the
-//           peptide's 32-bit counter (nb | ny | S) in an open-addressing
-//           table of kSlots 64-bit slots (offset << 32 | counter); a round has
-//           fewer than kSlots keys, so probing always ends;
+//           kRound candidates: the planes are scanned with the bitmaps,
+//           candidates counted and split into rounds of at most kRound
+//           candidates by runs of whole plane words; when the hot peaks alone
+//           can reach min_shared, the peptides of the segment no ordinary
+//           peak hit but with enough hot bits are scored here; otherwise
+//           there is one round of the twice plane;
+//   replay  per round, the log is walked; a candidate's record goes to its
+//           warp's queue, and full queues add (1 << 26 | iq) for a b ion or
+//           (1 << 20 | iq) for a y ion to the peptide's 32-bit counter (nb |
+//           ny | S) in an open-addressing table of kSlots 64-bit slots
+//           (offset << 32 | counter); a round has fewer than kSlots keys, so
+//           probing always ends;
 //   epilogue the occupied slots get the hot peaks' contributions from the
 //           bucket bitmaps; peptides with nb + ny >= min_shared are ranked
 //           with the exact key K = LF[nb] + LF[ny] + LS[S] and counted in the
@@ -37,9 +42,7 @@
 // The planes take 2 x 512 words per column of the super-chunk and the log
 // the words after them, so sparse spectra get wide super-chunks and dense
 // ones long logs.  A super-chunk whose planes and log do not fit is searched
-// column by column with 16384 directly indexed counters, and so is every
-// column of a unit whose spectrum has >= min_shared hot peaks (bitmaps alone
-// can qualify a peptide; that epilogue scans every counter and the bitmaps).
+// column by column with 16384 directly indexed counters.
 
 constexpr int kMaxHot = 6;                 // bitmap slices (b or y bitmap of a hot bucket) per spectrum
 constexpr int kMaxWarps = 16;              // CTAs of up to 512 threads
@@ -168,6 +171,7 @@ struct Layout {
     static_assert(kMaxRounds <= kRoundsCap, "round starts fit");
     static_assert(kMaxCols >= 1 && 2 * kMaxCols * kChunk / 32 < kListWord, "planes leave room for a log");
     static_assert(2 * kMaxCols * kChunk / 32 <= kChunk, "planes never reach the touched list");
+    static_assert(2 * kMaxCols * kChunk <= 0x80000u, "record offsets fit 19 bits below the peak index");
     static_assert(!kTouchDyn || kChunk + kTouchCap / 2 <= kListWord, "the touched list lies below the lists");
     static_assert(kDynWords >= kChunk, "the direct counters fit");
 };

@@ -14,7 +14,6 @@ namespace {
 constexpr int kPrepThreads = 256;
 constexpr int kPrepWarpPeaks = 256;        // spectra with at most this many raw peaks: one warp each
 constexpr int kPrepWarps = 8;              // spectra per block of prep_warp_kernel
-constexpr int kSearchThreads = 256;
 constexpr int kMinSegPids = (int)kChunk;  // smallest segment of a split window
 constexpr int kMaxSegs = 64;              // most segments a window is split into
 constexpr int kMergeWarps = 8;          // spectra per merge block
