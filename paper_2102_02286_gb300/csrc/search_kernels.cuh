@@ -406,9 +406,11 @@ __device__ __forceinline__ double warp_sum_f64(double v) {
 // over the list heads give the rows in rank order.  Lane l holds histogram
 // bins 8l .. 8l + 7.
 __global__ void __launch_bounds__(kMergeWarps * 32) merge_kernel(MergeArgs a) {
+    __shared__ int64_t gsurv[kMergeWarps][kHistBins + 1];   // the fit's survival function G[0..256]
     const int lane = threadIdx.x & 31;
     const uint32_t q = blockIdx.x * kMergeWarps + (threadIdx.x >> 5);
     if (q >= a.n) return;
+    int64_t* const G = gsurv[threadIdx.x >> 5];
     const uint32_t k = a.k;
     const uint64_t u0 = a.seg_off[q];
     const int nseg = (int)(a.seg_off[q + 1] - u0);
@@ -487,6 +489,13 @@ __global__ void __launch_bounds__(kMergeWarps * 32) merge_kernel(MergeArgs a) {
     }
     const int64_t G0 = __shfl_sync(0xffffffffu, above, 0);
     above -= run;           // lanes > lane
+    // G[j] in shared memory, so that the fit's points (a few bins next to
+    // one another) are spread one a lane and its FP64 logarithms run once
+    // for the warp rather than once per bin of a lane
+#pragma unroll
+    for (int i = 0; i < 8; ++i) G[8 * lane + i] = loc[i] + above;
+    if (lane == 0) G[kHistBins] = 0;
+    __syncwarp();
     const double dG0 = (double)G0;
     const int64_t key0 = __shfl_sync(0xffffffffu, row.key, 0);
     const uint32_t pid0 = __shfl_sync(0xffffffffu, row.pid, 0);
@@ -496,11 +505,9 @@ __global__ void __launch_bounds__(kMergeWarps * 32) merge_kernel(MergeArgs a) {
     if (weibull) {
         // R17: least squares of -ln(-ln F_j) on x = j + 1, F_j = 1 - G[j+1] / G[0],
         // over the bins with 0 < F_j < 1
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int j = 8 * lane + i;
-            const int64_t gn = loc[i] + above - g[i];   // G[j + 1]
-            if (have_top && gn > 0 && gn < G0) {
+        for (int j = lane; j < (int)kHistBins && have_top; j += 32) {
+            const int64_t gn = G[j + 1];
+            if (gn > 0 && gn < G0) {
                 const double x = (double)(j + 1);
                 const double y = -log(-log1p(-((double)gn / dG0)));
                 cn += 1.0;
@@ -527,11 +534,9 @@ __global__ void __launch_bounds__(kMergeWarps * 32) merge_kernel(MergeArgs a) {
         const int mode = bj;
         int64_t jtop = 0;
         if (have_top) { jtop = key0 >> 31; if (jtop > 255) jtop = 255; }
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int j = 8 * lane + i;
-            const int64_t gj = loc[i] + above;   // G[j]
-            if (have_top && j >= mode + 1 && j <= jtop - 1 && gj > 0) {
+        for (int j = mode + 1 + lane; j <= (int)jtop - 1 && have_top; j += 32) {
+            const int64_t gj = G[j];
+            if (gj > 0) {
                 const double x = (double)j;
                 const double y = log10((double)gj / dG0);
                 cn += 1.0;
