@@ -504,8 +504,9 @@ def run_serving(args):
                    "n_index_entries": int(st.n_entries), "index_bytes": int(st.device_bytes),
                    "index_build_s": t_index, "input_gen_s": t_gen, "pool_spectra": pool.n,
                    "batch_sizes": "log-uniform in [1, 4096]", "arrival_window_s": args.load_seconds,
-                   "server_slots": int(sstats.n_slots), "slot_bytes": int(sstats.slot_bytes),
-                   "server_launches": int(launches)},
+                   "server_streams": int(sstats.n_slots), "server_launches": int(launches),
+                   "pool_bytes": int(sstats.pool_bytes), "pool_peak_bytes": int(sstats.pool_peak),
+                   "memory_waits": int(sstats.memory_waits)},
         "loads": rows,
         "identical_results": identical,
     }
@@ -771,7 +772,9 @@ def extras(args, hc, torch):
     idx.close()
     out["serving_stream"] = {"workload": workload_desc(w), "pool_spectra": pool.n,
                              "batch_sizes": "log-uniform in [1, 4096]", "arrival_window_s": args.extra_load_seconds,
-                             "server_slots": int(sstats.n_slots), "server_launches": int(launches),
+                             "server_streams": int(sstats.n_slots), "server_launches": int(launches),
+                             "pool_bytes": int(sstats.pool_bytes), "pool_peak_bytes": int(sstats.pool_peak),
+                             "memory_waits": int(sstats.memory_waits),
                              "loads": rows, "identical_results": identical,
                              "wall_s": time.perf_counter() - t0}
     return out

@@ -220,6 +220,30 @@ hicops_status hicops_search(hicops_index* index, const hicops_batch* batch, hico
 hicops_status hicops_search_noalloc(hicops_index* index, const hicops_batch* batch, hicops_psm* out_psm,
                                     uint32_t* out_hist, uint32_t* out_nscored);
 
+/* hicops_search with its device scratch in caller memory.  No passage
+ * defines it: a memory-management addition of this library for callers that
+ * pool device memory themselves (the serving loop below admits its launches
+ * this way, by the bytes each one needs).
+ *   hicops_search_scratch_bytes: *out_bytes receives the scratch one search of
+ * n spectra takes on this index with its current launch shape (n = 0 counts
+ * as 1).  It depends on n alone, not on the spectra's peaks.
+ *   hicops_search_scratch: same search, results and output layout as
+ * hicops_search, for a batch whose buffers are all on the device
+ * (on_device = 1), with scratch a device buffer of scratch_bytes bytes that
+ * starts on a 256-byte boundary.  out_psm [n * top_k] is a device buffer;
+ * out_hist [n * 256] and out_nscored [n] are device buffers or NULL.  Work is
+ * enqueued on batch->cuda_stream and the call returns without waiting or
+ * allocating; the scratch must stay untouched until the stream has passed the
+ * search, and needs no clearing before it.  A change of the index's launch
+ * shape (hicops_index_set_config, hicops_autotune) can change the bytes.
+ * Errors: HICOPS_EINVAL (host pointers, NULL or misaligned scratch, the
+ * hicops_search cases), HICOPS_ENOMEM (scratch_bytes below what
+ * hicops_search_scratch_bytes gives for this n), HICOPS_ECUDA. */
+hicops_status hicops_search_scratch_bytes(const hicops_index* index, uint32_t n, uint64_t* out_bytes);
+hicops_status hicops_search_scratch(hicops_index* index, const hicops_batch* batch, void* scratch,
+                                    uint64_t scratch_bytes, hicops_psm* out_psm, uint32_t* out_hist,
+                                    uint32_t* out_nscored);
+
 /* Measurement helper: per spectrum, the precursor window [lo, hi) (Eq. 4's
  * filter_1), the number of retained peaks and the number of index entries
  * inside the window over the retained peaks' buckets (H(q), the work of
@@ -479,14 +503,23 @@ void hicops_plan_destroy(hicops_plan* plan);
 /* Serving loop (the paper's buffering and R/I/K pipeline of superstep 3,
  * Buffering and Task Scheduling sections, as a request server).  The index
  * stays resident; requests (batches of spectra in host memory) are copied at
- * submission and queued; a scheduler thread packs waiting requests into the
- * next launch on one of n_slots streams as soon as a slot is free, so
- * requests that arrive while others run are admitted as slots free up and
- * their work overlaps on the device.  Each slot owns a reusable plan for up
- * to slot_spectra spectra; slots are created while their scratch fits in
- * memory_budget bytes.  A request of more than slot_spectra spectra is
- * rejected (HICOPS_EINVAL).  Results do not depend on how requests are
- * packed.  Zero fields take the defaults (4 slots, 16 GiB, 32768 spectra). */
+ * submission and queued.  The server's device memory is one pool of
+ * memory_budget bytes, allocated at creation.  A scheduler thread packs the
+ * oldest waiting requests into one launch while that launch's block (its
+ * spectra, the search's scratch as hicops_search_scratch_bytes counts it,
+ * its PSM rows, histograms and counts) fits the pool's largest free range,
+ * and launches it on an idle stream; when the oldest request does not fit,
+ * it waits until launches in flight return their blocks.  Requests that
+ * arrive while others run are thus admitted as memory and streams free up,
+ * and their work overlaps on the device.  n_slots: launches in flight at
+ * most (one stream each); slot_spectra: spectra one launch packs at most;
+ * memory_budget: the pool's bytes.  A request of more than slot_spectra
+ * spectra, or whose launch alone would not fit the pool, is rejected at
+ * submission (HICOPS_EINVAL).  Results do not depend on how requests are
+ * packed.  The launch shape is the index's at creation.  Zero fields take the
+ * defaults (4 launches, 32768 spectra, 16 GiB).  Errors of create:
+ * HICOPS_EINVAL (a budget below one launch of one 512-peak spectrum),
+ * HICOPS_ENOMEM (the pool cannot be allocated), HICOPS_ECUDA. */
 typedef struct hicops_server_cfg {
     uint32_t n_slots;
     uint32_t slot_spectra;
@@ -495,9 +528,11 @@ typedef struct hicops_server_cfg {
 
 typedef struct hicops_server_stats {
     uint64_t submitted, completed, launches, spectra;
-    uint32_t n_slots;          /* slots actually created within the budget */
+    uint32_t n_slots;          /* launches in flight at most */
     uint32_t reserved;
-    uint64_t slot_bytes;       /* device scratch per slot */
+    uint64_t pool_bytes;       /* the device pool */
+    uint64_t pool_peak;        /* most pool bytes held by launches at once */
+    uint64_t memory_waits;     /* times the oldest request had to wait for pool memory */
 } hicops_server_stats;
 
 typedef struct hicops_server hicops_server;
@@ -521,11 +556,12 @@ hicops_status hicops_server_poll(hicops_server* srv, uint64_t ticket, int timeou
 hicops_status hicops_server_cancel(hicops_server* srv, uint64_t ticket);
 
 /* Counters of the server (requests submitted and completed, launches,
- * spectra, slots): the buffering section's queues observed.  Errors:
+ * spectra, pool use): the buffering section's queues observed.  Errors:
  * HICOPS_EINVAL (NULL). */
 hicops_status hicops_server_get_stats(hicops_server* srv, hicops_server_stats* out);
 
-/* Waits for launched work, drops queued requests, frees the slots. */
+/* Waits for launched work, drops queued requests, frees the pool and the
+ * streams. */
 void hicops_server_destroy(hicops_server* srv);
 
 /* Per-phase device time of the last hicops_search on this index, measured

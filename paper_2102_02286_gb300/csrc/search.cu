@@ -316,10 +316,105 @@ hicops_status stage_inputs(const hicops_batch* b, Scratch& sc, DevBatch& d) {
     return HICOPS_OK;
 }
 
+constexpr uint64_t align256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
+
+// alloc_workspace's allocators over caller memory.  Carve hands out
+// consecutive 256-byte aligned pieces of one buffer and fails when they would
+// not fit; Tally only adds up the bytes Carve would hand out.
+struct Carve {
+    unsigned char* base;
+    uint64_t cap, used;
+    template <class T>
+    cudaError_t get(T** p, uint64_t n) {
+        const uint64_t bytes = align256(sizeof(T) * (n ? n : 1));
+        if (used + bytes > cap) return cudaErrorMemoryAllocation;
+        *p = reinterpret_cast<T*>(base + used);
+        used += bytes;
+        return cudaSuccess;
+    }
+};
+
+struct Tally {
+    uint64_t used = 0;
+    template <class T>
+    cudaError_t get(T** p, uint64_t n) {
+        *p = nullptr;
+        used += align256(sizeof(T) * (n ? n : 1));
+        return cudaSuccess;
+    }
+};
+
+// The workspace of a search in caller memory: alloc_workspace's pieces
+// without the PSM rows (the caller always gives those), then a histogram and
+// candidate-count block for callers that pass none.
+template <class A>
+hicops_status scratch_workspace(A& al, const hicops_params& p, uint32_t n, uint32_t max_seg, Workspace& w) {
+    hicops_status st = alloc_workspace(al, p, n, max_seg, false, w);
+    if (st != HICOPS_OK) return st;
+    HC_CUDA(al.get(&w.hist, (uint64_t)n * kHistBins));
+    HC_CUDA(al.get(&w.ns, n));
+    return HICOPS_OK;
+}
+
 }  // namespace
+
+uint64_t scratch_bytes(const hicops_index* idx, const hicops_search_config& cfg, uint32_t n) {
+    if (!n) n = 1;
+    Tally t;
+    Workspace w;
+    scratch_workspace(t, idx->p, n, max_segments(cfg, n), w);
+    return t.used;
+}
+
+hicops_status search_in_scratch(hicops_index* idx, const hicops_batch* b, const hicops_search_config& cfg,
+                                void* scratch, uint64_t bytes, hicops_psm* out_psm, uint32_t* out_hist,
+                                uint32_t* out_nscored) {
+    hicops_status st = check_batch(idx, b);
+    if (st != HICOPS_OK) return st;
+    if (!b->on_device || !out_psm) {
+        set_error("a search in caller scratch takes device pointers (on_device = 1) and a device out_psm");
+        return HICOPS_EINVAL;
+    }
+    if (!scratch || (reinterpret_cast<uintptr_t>(scratch) & 255u)) {
+        set_error("scratch must be a 256-byte aligned device pointer");
+        return HICOPS_EINVAL;
+    }
+    const uint32_t n = b->n;
+    if (n == 0) return HICOPS_OK;
+    const uint64_t need = scratch_bytes(idx, cfg, n);
+    if (bytes < need) {
+        set_error("scratch of %llu bytes; a search of %u spectra needs %llu", (unsigned long long)bytes, n,
+                  (unsigned long long)need);
+        return HICOPS_ENOMEM;
+    }
+    Carve cv{static_cast<unsigned char*>(scratch), bytes, 0};
+    Workspace w;
+    st = scratch_workspace(cv, idx->p, n, max_segments(cfg, n), w);
+    if (st != HICOPS_OK) return st;
+    const DevBatch d{b->peak_off, b->mz, b->intensity, b->prec_mz, b->charge, b->prec_tol_da};
+    return enqueue_search(idx, d, n, w, cfg, out_psm, out_hist ? out_hist : w.hist, out_nscored ? out_nscored : w.ns,
+                          (cudaStream_t)b->cuda_stream, false);
+}
+
 }  // namespace hicops
 
 using namespace hicops;
+
+extern "C" hicops_status hicops_search_scratch_bytes(const hicops_index* idx, uint32_t n, uint64_t* out_bytes) {
+    if (!idx || !out_bytes) { set_error("NULL argument"); return HICOPS_EINVAL; }
+    if (!idx->dev.ready) { set_error("index has no device part (call hicops_index_upload)"); return HICOPS_EINVAL; }
+    hicops_status st = sm_count();
+    if (st != HICOPS_OK) return st;
+    *out_bytes = scratch_bytes(idx, idx->dev.cfg, n);
+    return HICOPS_OK;
+}
+
+extern "C" hicops_status hicops_search_scratch(hicops_index* idx, const hicops_batch* b, void* scratch,
+                                               uint64_t bytes, hicops_psm* out_psm, uint32_t* out_hist,
+                                               uint32_t* out_nscored) {
+    if (!idx) { set_error("NULL argument"); return HICOPS_EINVAL; }
+    return search_in_scratch(idx, b, idx->dev.cfg, scratch, bytes, out_psm, out_hist, out_nscored);
+}
 
 struct hicops_plan {
     hicops_index* idx = nullptr;
@@ -589,7 +684,6 @@ namespace {
 
 constexpr uint32_t kNoAllocSegs = 16;      // work units per spectrum at most
 constexpr int kNoAllocDevices = 64;        // device ordinals served
-constexpr uint64_t align256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
 
 // Workspace bytes for cap spectra at the largest top_n_peaks and top_k, in
 // alloc_workspace's order (each piece 256-byte aligned), plus room for the
@@ -665,21 +759,6 @@ hicops_status noalloc_scratch(int dev, unsigned char** out) {
     *out = static_cast<unsigned char*>(g_noalloc_base[dev]);
     return HICOPS_OK;
 }
-
-// alloc_workspace's allocator over the fixed array: hands out consecutive
-// 256-byte aligned pieces and fails when they would not fit.
-struct Carve {
-    unsigned char* base;
-    uint64_t cap, used;
-    template <class T>
-    cudaError_t get(T** p, uint64_t n) {
-        const uint64_t bytes = align256(sizeof(T) * (n ? n : 1));
-        if (used + bytes > cap) return cudaErrorMemoryAllocation;
-        *p = reinterpret_cast<T*>(base + used);
-        used += bytes;
-        return cudaSuccess;
-    }
-};
 
 }  // namespace
 }  // namespace hicops

@@ -74,7 +74,7 @@ class ServerCfg(C.Structure):
 class ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("launches", C.c_uint64),
                 ("spectra", C.c_uint64), ("n_slots", C.c_uint32), ("reserved", C.c_uint32),
-                ("slot_bytes", C.c_uint64)]
+                ("pool_bytes", C.c_uint64), ("pool_peak", C.c_uint64), ("memory_waits", C.c_uint64)]
 
 
 class Timing(C.Structure):
@@ -127,6 +127,8 @@ def load(build_if_missing: bool = False):
         "hicops_build_index": (st, [C.POINTER(Proteins), P, C.c_uint32, C.POINTER(Params), C.POINTER(P)]),
         "hicops_search": (st, [P, C.POINTER(Batch), P, P, P]),
         "hicops_search_noalloc": (st, [P, C.POINTER(Batch), P, P, P]),
+        "hicops_search_scratch_bytes": (st, [P, C.c_uint32, C.POINTER(C.c_uint64)]),
+        "hicops_search_scratch": (st, [P, C.POINTER(Batch), P, C.c_uint64, P, P, P]),
         "hicops_search_work": (st, [P, C.POINTER(Batch), P, P, P, P]),
         "hicops_index_set_config": (st, [P, C.POINTER(SearchConfig)]),
         "hicops_autotune": (st, [P, C.POINTER(Batch), C.POINTER(SearchConfig), C.POINTER(C.c_double)]),
@@ -382,6 +384,21 @@ class Index:
         """hicops_search_noalloc: device tensors, at most NOALLOC_MAX_SPECTRA spectra, no allocation."""
         b = _device_batch_struct(dev_batch, stream)
         _check(load().hicops_search_noalloc(self.h, C.byref(b), out.psm.data_ptr(),
+                                            out.hist.data_ptr() if out.hist is not None else None,
+                                            out.n_scored.data_ptr() if out.n_scored is not None else None))
+
+
+    def search_scratch_bytes(self, n: int) -> int:
+        """hicops_search_scratch_bytes: device scratch one search of n spectra takes."""
+        b = C.c_uint64()
+        _check(load().hicops_search_scratch_bytes(self.h, n, C.byref(b)))
+        return b.value
+
+    def search_scratch(self, dev_batch: "DeviceBatch", out: "DeviceResult", scratch, nbytes=None, stream=None):
+        """hicops_search_scratch: device tensors, scratch a device tensor (256-byte aligned start)."""
+        b = _device_batch_struct(dev_batch, stream)
+        nbytes = scratch.numel() * scratch.element_size() if nbytes is None else nbytes
+        _check(load().hicops_search_scratch(self.h, C.byref(b), scratch.data_ptr(), nbytes, out.psm.data_ptr(),
                                             out.hist.data_ptr() if out.hist is not None else None,
                                             out.n_scored.data_ptr() if out.n_scored is not None else None))
 

@@ -1,5 +1,5 @@
-"""The serving loop: continuous batching across slots; every request's
-result is the same alone and in the mix."""
+"""The serving loop: continuous batching over a device-memory pool and several
+streams; every request's result is the same alone and in the mix."""
 import threading
 import time
 
@@ -146,4 +146,42 @@ def test_errors_and_cancel(setup):
         assert srv.poll(ts[-1], timeout_ms=120000) is not None
     srv.close()
     with pytest.raises(hc.HicopsError):
-        hc.Server(idx, n_slots=2, slot_spectra=1024, memory_budget=1024)   # budget below one slot
+        hc.Server(idx, n_slots=2, slot_spectra=1024, memory_budget=1024)   # budget below one launch
+
+
+def test_admission_by_device_memory(setup):
+    """A pool that holds about one and a half of the largest request's
+    launches: requests wait for memory that launches in flight give back (the
+    server counts the waits), the pool never holds more than its size, every
+    result is the one the request gets alone, and a request whose launch
+    alone exceeds the pool is refused at submission."""
+    w, idx, spec = setup
+    k = w.params.top_k
+    rng = np.random.default_rng(3)
+    reqs = split_requests(spec.n, rng, max_size=64)
+    alone = [idx.search(spec.subset(range(a, b))) for a, b in reqs]
+
+    def launch_bound(a, b):
+        # the search's scratch, the spectra, the PSM rows, histograms and
+        # counts, and the 256-byte rounding of each piece
+        n, npk = b - a, int(spec.peak_off[b] - spec.peak_off[a])
+        return (idx.search_scratch_bytes(n) + 8 * (n + 1) + 8 * npk + 17 * n + n * (32 * k + 4 * 256 + 4)
+                + 9 * 256)
+
+    budget = 3 * max(launch_bound(a, b) for a, b in reqs) // 2
+    srv = hc.Server(idx, n_slots=3, slot_spectra=256, memory_budget=budget)
+    tickets = [srv.submit(spec.subset(range(a, b))) for a, b in reqs]
+    for t, ref in zip(tickets, alone):
+        got = srv.poll(t, timeout_ms=120000)
+        assert got is not None
+        np.testing.assert_array_equal(got.psm, ref.psm)
+        np.testing.assert_array_equal(got.hist, ref.hist)
+        np.testing.assert_array_equal(got.n_scored, ref.n_scored)
+    st = srv.stats()
+    assert st.completed == len(reqs) and st.spectra == spec.n
+    assert 0 < st.pool_peak <= st.pool_bytes <= budget
+    assert st.memory_waits > 0
+    with pytest.raises(hc.HicopsError) as e:
+        srv.submit(spec.subset(range(256)))
+    assert e.value.status == hc.EINVAL and "pool" in str(e.value)
+    srv.close()
