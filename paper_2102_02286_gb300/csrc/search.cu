@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "search_kernels.cuh"
+#include "search_scratch.h"
 
 namespace hicops {
 

@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "dev_common.cuh"
+#include "search_scratch.h"
 
 namespace {
 
