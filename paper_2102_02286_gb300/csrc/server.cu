@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "dev_common.cuh"
+#include "pool_map.h"
 #include "search_scratch.h"
 
 namespace {
@@ -65,54 +66,6 @@ struct Pinned {
 
 constexpr uint64_t piece(uint64_t bytes) { return (std::max<uint64_t>(bytes, 1) + 255) & ~uint64_t(255); }
 
-// First-fit allocator over the byte offsets of the device pool.  Free ranges
-// are kept by offset and are never adjacent: a returned range merges with
-// its free neighbours.  Sizes are multiples of 256.
-struct PoolMap {
-    std::map<uint64_t, uint64_t> free_ranges;   // offset -> size
-    uint64_t size = 0, used = 0, peak = 0;
-    void init(uint64_t bytes) {
-        size = bytes;
-        free_ranges.clear();
-        if (bytes) free_ranges[0] = bytes;
-    }
-    uint64_t largest() const {
-        uint64_t m = 0;
-        for (const auto& f : free_ranges) m = std::max(m, f.second);
-        return m;
-    }
-    bool take(uint64_t bytes, uint64_t* off) {
-        for (auto it = free_ranges.begin(); it != free_ranges.end(); ++it) {
-            if (it->second < bytes) continue;
-            *off = it->first;
-            const uint64_t rest = it->second - bytes;
-            free_ranges.erase(it);
-            if (rest) free_ranges[*off + bytes] = rest;
-            used += bytes;
-            peak = std::max(peak, used);
-            return true;
-        }
-        return false;
-    }
-    void give(uint64_t off, uint64_t bytes) {
-        used -= bytes;
-        auto next = free_ranges.lower_bound(off);
-        if (next != free_ranges.begin()) {
-            auto prev = std::prev(next);
-            if (prev->first + prev->second == off) {
-                off = prev->first;
-                bytes += prev->second;
-                free_ranges.erase(prev);
-            }
-        }
-        if (next != free_ranges.end() && off + bytes == next->first) {
-            bytes += next->second;
-            free_ranges.erase(next);
-        }
-        free_ranges[off] = bytes;
-    }
-};
-
 // One launch in flight at a time: its stream, its event, the pinned staging
 // of its spectra and results, and its block of the pool.
 struct Lane {
@@ -142,7 +95,7 @@ struct hicops_server {
     uint32_t k = 0;
     hicops_search_config cfg{};      // launch shape, fixed at creation
     unsigned char* pool = nullptr;   // device pool of map.size bytes
-    PoolMap map;
+    hicops::PoolMap map;
     std::vector<std::unique_ptr<Lane>> lanes;
     std::mutex mu;
     std::condition_variable cv_sched;   // queue, lanes or pool changed
