@@ -123,9 +123,12 @@ typedef struct hicops_proteins {
  * are ready when the stream reaches that point).  on_device = 0: host
  * pointers; the call copies inputs in and results out and returns after the
  * results are in the caller's buffers.  A spectrum may hold any number of
- * raw peaks.  Invalid spectra (charge 0, non-finite precursor, negative
- * tolerance, no peak inside [frag_mz_min, frag_mz_max)) do not fail the
- * batch: their rows are padding and their histogram is empty. */
+ * raw peaks.  mz and intensity hold at least peak_off[n] entries (device
+ * batches: the entries [peak_off[0], peak_off[n]) are the batch's).
+ * Invalid spectra (charge 0, non-finite precursor, negative tolerance, no
+ * peak inside [frag_mz_min, frag_mz_max), peak offsets that decrease or leave
+ * [peak_off[0], peak_off[n])) do not fail the batch: their rows are padding,
+ * their histogram is empty, and none of their peaks is read. */
 typedef struct hicops_batch {
     uint32_t n;
     uint32_t on_device;
@@ -540,7 +543,10 @@ typedef struct hicops_server hicops_server;
 hicops_status hicops_server_create(hicops_index* index, const hicops_server_cfg* cfg, hicops_server** out);
 
 /* Queues a request (batch in host memory, on_device = 0; the arrays are
- * copied before the call returns).  *ticket identifies it for poll/cancel. */
+ * copied before the call returns).  *ticket identifies it for poll/cancel.
+ * Errors: HICOPS_EINVAL (NULL pointers, device pointers, 0 or more than
+ * slot_spectra spectra, peak offsets that decrease, a launch larger than
+ * the pool). */
 hicops_status hicops_server_submit(hicops_server* srv, const hicops_batch* batch, uint64_t* ticket);
 
 /* Waits up to timeout_ms (0 = do not wait, < 0 = wait forever) for the

@@ -95,12 +95,15 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(PrepArgs a) {
     __shared__ int s_nrep;
     const uint32_t q = blockIdx.x;
     const uint64_t p0 = a.peak_off[q], p1 = a.peak_off[q + 1];
-    const uint64_t cnt = p1 >= p0 ? p1 - p0 : 0;
+    // a spectrum's peaks lie inside the batch's [peak_off[0], peak_off[n]),
+    // else it is invalid and nothing of it is read
+    const bool inside = p0 <= p1 && p0 >= a.peak_off[0] && p1 <= a.peak_off[a.n];
+    const uint64_t cnt = inside ? p1 - p0 : 0;
     if (cnt <= (uint64_t)kPrepWarpPeaks) return;   // prep_warp_kernel's spectra
     const double prec = a.prec_mz[q];
     const double tol = a.tol[q];
     const uint32_t z = a.charge[q];
-    bool valid = p1 >= p0 && z > 0 && isfinite(prec) && isfinite(tol) && tol >= 0.0;
+    bool valid = inside && z > 0 && isfinite(prec) && isfinite(tol) && tol >= 0.0;
     int keep = 0;
     if (valid && cnt > 0) {
         for (uint64_t base = 0; base < cnt; base += kPrepChunk) {
@@ -202,12 +205,13 @@ __global__ void __launch_bounds__(kPrepWarps * 32) prep_warp_kernel(PrepArgs a) 
     if (q >= a.n) return;
     uint64_t* keys = keys_all[wi];
     const uint64_t p0 = a.peak_off[q], p1 = a.peak_off[q + 1];
-    const uint64_t cnt = p1 >= p0 ? p1 - p0 : 0;
+    const bool inside = p0 <= p1 && p0 >= a.peak_off[0] && p1 <= a.peak_off[a.n];   // as in prep_kernel
+    const uint64_t cnt = inside ? p1 - p0 : 0;
     if (cnt > (uint64_t)kPrepWarpPeaks) return;   // prep_kernel's spectra
     const double prec = a.prec_mz[q];
     const double tol = a.tol[q];
     const uint32_t z = a.charge[q];
-    bool valid = p1 >= p0 && z > 0 && isfinite(prec) && isfinite(tol) && tol >= 0.0;
+    bool valid = inside && z > 0 && isfinite(prec) && isfinite(tol) && tol >= 0.0;
     int keep = 0;
     if (valid && cnt > 0) {
         const int npow = next_pow2((int)cnt);

@@ -368,8 +368,13 @@ extern "C" hicops_status hicops_server_submit(hicops_server* srv, const hicops_b
     if (b->on_device) { set_error("server requests are host batches (on_device = 0)"); return HICOPS_EINVAL; }
     if (b->n == 0 || b->n > srv->cap) { set_error("request of %u spectra (1..%u)", b->n, srv->cap); return HICOPS_EINVAL; }
     if (!b->peak_off || !b->prec_mz || !b->charge || !b->prec_tol_da) { set_error("batch pointers are NULL"); return HICOPS_EINVAL; }
-    auto r = std::make_shared<Request>();
     const uint32_t n = b->n;
+    for (uint32_t i = 0; i < n; ++i)
+        if (b->peak_off[i + 1] < b->peak_off[i]) {
+            set_error("peak offsets decrease at spectrum %u", i);
+            return HICOPS_EINVAL;
+        }
+    auto r = std::make_shared<Request>();
     r->n = n;
     const uint64_t base = b->peak_off[0];
     r->peak_off.resize(n + 1);

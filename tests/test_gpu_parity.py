@@ -1,5 +1,7 @@
 """GPU parity: the CUDA path through the C ABI against the CPU oracle on the
 same seeded inputs."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -194,6 +196,35 @@ def test_edge_cases(gpu, oracle_lib):
         assert got.n_scored[q] >= 1, q
     # the last spectrum retains the peptide's own peaks, so it finds what the first finds
     assert got.psm["pid"][12][0] == got.psm["pid"][0][0]
+
+
+def test_malformed_peak_offsets(gpu):
+    """Spectra whose peak offsets decrease or leave the batch's
+    [peak_off[0], peak_off[n]) are invalid: padding rows, an empty
+    histogram, none of their peaks read; their neighbours are searched as in
+    a well-formed batch, through host and device buffers."""
+    w = configs.TINY_CLOSED.with_proteins(80)
+    prot = synth.make_proteome(w.n_proteins, w.seed)
+    idx = hc.Index(prot.seq, prot.off, w.mods, w.params)
+    good = synth.make_spectra(prot, w, n=4)
+    ref = idx.search(good)
+    off = good.peak_off.astype(np.uint64).copy()
+    # spectrum 1 ends past peak_off[n]; spectrum 2 starts there and ends lower
+    off[2] = off[4] + 1000
+    bad = dataclasses.replace(good, peak_off=off)
+    for got in (idx.search(bad), _search_device(gpu, idx, bad, w.params.top_k)):
+        for q in (1, 2):
+            assert np.all(got.psm["pid"][q] == PAD) and got.n_scored[q] == 0 and got.hist[q].sum() == 0
+        for q in (0, 3):
+            np.testing.assert_array_equal(got.psm[q], ref.psm[q])
+            np.testing.assert_array_equal(got.hist[q], ref.hist[q])
+
+
+def _search_device(gpu, idx, spec, k):
+    out = hc.DeviceResult.alloc(spec.n, k)
+    idx.search_device(hc.DeviceBatch.from_spectra(spec), out)
+    gpu.cuda.synchronize()
+    return out.to_host(spec.n, k)
 
 
 def test_empty_batch(gpu):

@@ -1,5 +1,6 @@
 """The serving loop: continuous batching over a device-memory pool and several
 streams; every request's result is the same alone and in the mix."""
+import dataclasses
 import threading
 import time
 
@@ -147,6 +148,15 @@ def test_errors_and_cancel(setup):
     srv.close()
     with pytest.raises(hc.HicopsError):
         hc.Server(idx, n_slots=2, slot_spectra=1024, memory_budget=1024)   # budget below one launch
+    # peak offsets that decrease are refused at submission
+    srv = hc.Server(idx, n_slots=1, slot_spectra=32)
+    sub = spec.subset(range(4))
+    off = sub.peak_off.astype(np.uint64).copy()
+    off[2] = off[4] + 1000
+    with pytest.raises(hc.HicopsError) as e:
+        srv.submit(dataclasses.replace(sub, peak_off=off))
+    assert e.value.status == hc.EINVAL and "decrease" in str(e.value)
+    srv.close()
 
 
 def test_admission_by_device_memory(setup):
