@@ -480,7 +480,12 @@ class DeviceResult:
 
 
 class Server:
-    """Continuous-batching request server over a resident index."""
+    """Continuous-batching request server over a resident index.
+
+    n_slots: launches in flight at most (one stream each); slot_spectra:
+    spectra one launch packs at most; memory_budget: bytes of the device pool
+    that launches take their blocks from (requests wait for pool memory).
+    Zero takes the library's default."""
 
     def __init__(self, index: Index, n_slots: int = 0, slot_spectra: int = 0, memory_budget: int = 0):
         self.index = index
