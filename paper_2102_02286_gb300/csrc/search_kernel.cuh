@@ -749,8 +749,9 @@ __global__ void __launch_bounds__(THREADS, THREADS <= 384 ? 2 : 1) search_kernel
                 if (w < warp) run += sh.wcand[w];
                 total += sh.wcand[w];
             }
-            // round r holds the words with r * kRound <= candidates-before < (r + 1) * kRound
-            for (uint32_t i0 = 0; i0 < wpw; i0 += 32) {
+            // round r holds the words with r * kRound <= candidates-before < (r + 1) * kRound;
+            // one round (the common case) starts at word 0 and needs no scan
+            for (uint32_t i0 = 0; total > kRound && i0 < wpw; i0 += 32) {
                 const uint32_t w = wbeg + i0 + lane;
                 const uint32_t cw = __popc(twice[w]);
                 uint32_t incl = cw;
