@@ -515,13 +515,14 @@ void hicops_plan_destroy(hicops_plan* plan);
  * it waits until launches in flight return their blocks.  Requests that
  * arrive while others run are thus admitted as memory and streams free up,
  * and their work overlaps on the device.  n_slots: launches in flight at
- * most (one stream each); slot_spectra: spectra one launch packs at most;
+ * most (one stream each, 1..64); slot_spectra: spectra one launch packs at most;
  * memory_budget: the pool's bytes.  A request of more than slot_spectra
  * spectra, or whose launch alone would not fit the pool, is rejected at
  * submission (HICOPS_EINVAL).  Results do not depend on how requests are
  * packed.  The launch shape is the index's at creation.  Zero fields take the
  * defaults (4 launches, 32768 spectra, 16 GiB).  Errors of create:
- * HICOPS_EINVAL (a budget below one launch of one 512-peak spectrum),
+ * HICOPS_EINVAL (n_slots above 64, a budget below one launch of one
+ * 512-peak spectrum),
  * HICOPS_ENOMEM (the pool cannot be allocated), HICOPS_ECUDA. */
 typedef struct hicops_server_cfg {
     uint32_t n_slots;

@@ -64,6 +64,8 @@ struct Pinned {
     ~Pinned() { if (p) cudaFreeHost(p); }
 };
 
+constexpr uint32_t kMaxLanes = 64;   // launches in flight at most (n_slots)
+
 constexpr uint64_t piece(uint64_t bytes) { return (std::max<uint64_t>(bytes, 1) + 255) & ~uint64_t(255); }
 
 // One launch in flight at a time: its stream, its event, the pinned staging
@@ -320,6 +322,10 @@ extern "C" hicops_status hicops_server_create(hicops_index* idx, const hicops_se
     if (!cfg.n_slots) cfg.n_slots = 4;
     if (!cfg.slot_spectra) cfg.slot_spectra = 32768;
     if (!cfg.memory_budget) cfg.memory_budget = 16ull << 30;
+    if (cfg.n_slots > kMaxLanes) {   // each costs a stream, a thread and pinned staging
+        set_error("n_slots must be at most %u", kMaxLanes);
+        return HICOPS_EINVAL;
+    }
     HC_CUDA(cudaSetDevice(idx->dev.device));
     uint64_t probe = 0;
     hicops_status st = hicops_search_scratch_bytes(idx, 1, &probe);   // also learns the SM count

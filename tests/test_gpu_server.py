@@ -148,6 +148,9 @@ def test_errors_and_cancel(setup):
     srv.close()
     with pytest.raises(hc.HicopsError):
         hc.Server(idx, n_slots=2, slot_spectra=1024, memory_budget=1024)   # budget below one launch
+    with pytest.raises(hc.HicopsError) as e:
+        hc.Server(idx, n_slots=65)                                           # more launches in flight than allowed
+    assert e.value.status == hc.EINVAL
     # peak offsets that decrease are refused at submission
     srv = hc.Server(idx, n_slots=1, slot_spectra=32)
     sub = spec.subset(range(4))
