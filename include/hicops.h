@@ -257,7 +257,7 @@ hicops_status hicops_search_work(hicops_index* index, const hicops_batch* batch,
 
 /* Sizes of the index: P and the unmodified sequences (Notation section: the
  * database of D = zeta * 2^m entries), the fragment-index entries and bins
- * (Superstep 1 items 2-3), device bytes and build times.  The survey's name
+ * (Superstep 1 items 2-3), device bytes and build times.  The name
  * hicops_index_stats is the struct's; the call carries get_ so the two do
  * not collide in C.  Errors: HICOPS_EINVAL (NULL). */
 hicops_status hicops_index_get_stats(const hicops_index* index, hicops_index_stats* out);
